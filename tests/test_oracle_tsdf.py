@@ -1,0 +1,137 @@
+"""Pins of the oracle's Eq. 1 samples against closed forms (no GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import morton, tsdf
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def _camera(R=np.eye(3), C=(0.0, 0.0, 0.0)):
+    pose = np.eye(4)
+    pose[:3, :3] = R
+    pose[:3, 3] = C
+    return pose
+
+
+def _rot(seed):
+    q, _ = np.linalg.qr(np.random.default_rng(seed).normal(size=(3, 3)))
+    return q * np.sign(np.linalg.det(q))
+
+
+def test_morton_bits():
+    assert morton.encode(1, 0, 0, 4) == 1
+    assert morton.encode(0, 1, 0, 4) == 2
+    assert morton.encode(0, 0, 1, 4) == 4
+    assert morton.encode(1, 1, 1, 4) == 7
+    assert morton.encode(2, 0, 0, 4) == 8
+    assert morton.encode(15, 15, 15, 4) == 4095
+    rng = np.random.default_rng(0)
+    x, y, z = rng.integers(0, 512, size=(3, 1000))
+    assert all(np.array_equal(a, b) for a, b in zip(morton.decode(morton.encode(x, y, z, 9), 9), (x, y, z)))
+
+
+def test_centres_closed_form():
+    # level-1 node at corner (2, 0, 2) of a 4^3 grid over [-1, 1]^3: edge 2 voxels = 1 m
+    k = morton.encode(2, 0, 2, 2)
+    c = tsdf.centres(np.array([k]), np.array([1]), [-1.0, -1.0, -1.0], 2.0, 2)
+    assert np.allclose(c, [[0.5, -0.5, 0.5]], atol=0, rtol=0)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_plane_on_pixel_rays(seed):
+    """Fronto-parallel plane at z-depth Z0: a point at z-depth t on the ray
+    through a pixel centre has phi = (Z0 - t) |K^-1 (px+.5, py+.5, 1)|."""
+    H, W, fx, fy, cx, cy, Z0, delta, eta = 24, 32, 40.0, 50.0, 15.0, 11.0, 2.0, 0.05, 0.1
+    R = _rot(seed)
+    C = np.array([0.3, -0.2, 0.1])
+    depth = np.full((1, H, W), Z0, np.float32)
+    rng = np.random.default_rng(seed)
+    px, py = rng.integers(0, W, 200), rng.integers(0, H, 200)
+    t = rng.uniform(1.8, 2.2, 200)
+    a, b = (px + 0.5 - cx) / fx, (py + 0.5 - cy) / fy
+    xcam = np.stack([a * t, b * t, t], 1)
+    pts = xcam @ R.T + C
+    f = tsdf.samples(pts, depth, np.array([[fx, fy, cx, cy]]), _camera(R, C)[None], delta, eta)[:, 0]
+    phi = (Z0 - t) * np.sqrt(a * a + b * b + 1.0)
+    expect = np.where(phi >= -eta, np.clip(phi / delta, -1, 1), np.nan)
+    np.testing.assert_allclose(f, expect, rtol=0, atol=1e-9)
+    assert np.array_equal(np.isnan(f), phi < -eta)
+
+
+def test_sphere_range_on_pixel_rays():
+    """Sphere of radius r at distance L on the optical axis: the range along a
+    pixel-centre ray is the near root of the ray-sphere quadratic."""
+    H, W, f_, r, L, delta = 20, 20, 30.0, 0.5, 3.0, 0.2
+    cx = cy = 10.0
+    px, py = np.meshgrid(np.arange(W), np.arange(H))
+    a, b = (px + 0.5 - cx) / f_, (py + 0.5 - cy) / f_
+    n = np.sqrt(a * a + b * b + 1)
+    # unit ray e = (a, b, 1)/n, |s e - (0,0,L)|^2 = r^2
+    bq = -2 * L / n
+    disc = bq * bq - 4 * (L * L - r * r)
+    rng_hit = np.where(disc >= 0, (-bq - np.sqrt(np.maximum(disc, 0))) / 2, np.inf)
+    depth = (rng_hit / n).astype(np.float32)[None]       # z-depth
+    sel = np.argwhere(np.isfinite(rng_hit))
+    s = rng_hit[sel[:, 0], sel[:, 1]] + 0.01
+    e = np.stack([a[sel[:, 0], sel[:, 1]], b[sel[:, 0], sel[:, 1]], np.ones(len(sel))], 1) / n[sel[:, 0], sel[:, 1], None]
+    pts = e * s[:, None]
+    out = tsdf.samples(pts, depth, np.array([[f_, f_, cx, cy]]), _camera()[None], delta, 1.0)[:, 0]
+    d32 = depth[0][sel[:, 0], sel[:, 1]].astype(np.float64) * n[sel[:, 0], sel[:, 1]]
+    np.testing.assert_allclose(out, np.clip((d32 - s) / delta, -1, 1), atol=1e-12)
+    np.testing.assert_allclose(out, -0.05, atol=5e-6)     # float32 depth rounding only
+
+
+def test_visibility_rules():
+    H, W, f_ = 4, 4, 2.0
+    depth = np.full((1, H, W), 1.0, np.float32)
+    depth[0, 0, 0] = 0.0
+    depth[0, 0, 1] = np.nan
+    depth[0, 0, 2] = np.inf
+    depth[0, 0, 3] = -1.0
+    intr = np.array([[f_, f_, 2.0, 2.0]])
+    pose = _camera()[None]
+
+    def ray(px, py, t):
+        return np.array([[(px + 0.5 - 2.0) / f_ * t, (py + 0.5 - 2.0) / f_ * t, t]])
+
+    s = lambda p, eta=0.5: tsdf.samples(p, depth, intr, pose, 0.1, eta)[0, 0]
+    assert np.isnan(s(ray(0, 0, 0.5)))           # depth 0: invalid
+    assert np.isnan(s(ray(1, 0, 0.5)))           # NaN depth: invalid
+    assert s(ray(2, 0, 0.5)) == 1.0              # ray miss: free space
+    assert np.isnan(s(ray(3, 0, 0.5)))           # negative depth: invalid
+    assert s(ray(1, 1, 0.5)) == 1.0              # in front, beyond delta
+    assert s(ray(1, 1, 1.2)) == -1.0             # behind, within eta
+    assert np.isnan(s(ray(1, 1, 1.2), eta=0.1))  # behind beyond eta: unseen
+    assert np.isnan(s(np.array([[0.0, 0.0, -1.0]])))   # behind the camera
+    assert np.isnan(s(np.array([[10.0, 0.0, 1.0]])))   # outside the image
+    assert np.isnan(s(np.array([[0.0, 0.0, 0.0]])))    # on the camera centre
+
+
+def test_rigid_motion_invariance():
+    """Moving camera and points by one rigid motion leaves f unchanged."""
+    rng = np.random.default_rng(3)
+    depth = rng.uniform(1.0, 2.0, (2, 16, 16)).astype(np.float32)
+    intr = np.array([[20.0, 20.0, 8.0, 8.0]] * 2)
+    pose = np.stack([_camera(_rot(1), (0, 0, 0)), _camera(_rot(2), (0.1, 0, 0))])
+    pts = rng.uniform(-1, 1, (500, 3))
+    f0 = tsdf.samples(pts, depth, intr, pose, 0.2, 0.4)
+    R0, t0 = _rot(7), np.array([1.0, 2.0, -3.0])
+    pose2 = pose.copy()
+    for i in range(2):
+        pose2[i, :3, :3] = R0 @ pose[i, :3, :3]
+        pose2[i, :3, 3] = R0 @ pose[i, :3, 3] + t0
+    f1 = tsdf.samples(pts @ R0.T + t0, depth, intr, pose2, 0.2, 0.4)
+    same = np.isnan(f0) == np.isnan(f1)
+    assert same.mean() > 0.99          # pixel choice may flip exactly on a pixel border
+    ok = same & ~np.isnan(f0)
+    assert np.mean(np.abs(f0[ok] - f1[ok]) < 1e-9) > 0.99
+
+
+def test_median_rule():
+    fs = np.array([[0.1, 0.5, np.nan, np.nan], [0.1, 0.3, 0.9, np.nan],
+                   [np.nan] * 4, [-0.2, 0.0, 0.4, 1.0]])
+    W = np.array([2, 3, 0, 4])
+    np.testing.assert_allclose(tsdf.median(fs, W), [0.3, 0.3, -1.0, 0.2])
