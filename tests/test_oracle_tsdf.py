@@ -37,7 +37,7 @@ def test_centres_closed_form():
     # level-1 node at corner (2, 0, 2) of a 4^3 grid over [-1, 1]^3: edge 2 voxels = 1 m
     k = morton.encode(2, 0, 2, 2)
     c = tsdf.centres(np.array([k]), np.array([1]), [-1.0, -1.0, -1.0], 2.0, 2)
-    assert np.allclose(c, [[0.5, -0.5, 0.5]], atol=0, rtol=0)
+    assert c.dtype == np.float32 and np.array_equal(c, np.array([[0.5, -0.5, 0.5]], np.float32))
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
@@ -57,7 +57,9 @@ def test_plane_on_pixel_rays(seed):
     f = tsdf.samples(pts, depth, np.array([[fx, fy, cx, cy]]), _camera(R, C)[None], delta, eta)[:, 0]
     phi = (Z0 - t) * np.sqrt(a * a + b * b + 1.0)
     expect = np.where(phi >= -eta, np.clip(phi / delta, -1, 1), np.nan)
-    np.testing.assert_allclose(f, expect, rtol=0, atol=1e-9)
+    # float32 evaluation: about six roundings of magnitude ~2 m (ulp 2.4e-7)
+    # divided by delta = 0.05 bound the error by ~3e-5 in truncation units
+    np.testing.assert_allclose(f, expect, rtol=0, atol=3e-5)
     assert np.array_equal(np.isnan(f), phi < -eta)
 
 
@@ -80,8 +82,9 @@ def test_sphere_range_on_pixel_rays():
     pts = e * s[:, None]
     out = tsdf.samples(pts, depth, np.array([[f_, f_, cx, cy]]), _camera()[None], delta, 1.0)[:, 0]
     d32 = depth[0][sel[:, 0], sel[:, 1]].astype(np.float64) * n[sel[:, 0], sel[:, 1]]
-    np.testing.assert_allclose(out, np.clip((d32 - s) / delta, -1, 1), atol=1e-12)
-    np.testing.assert_allclose(out, -0.05, atol=5e-6)     # float32 depth rounding only
+    # float32 arithmetic on ranges near 2.6 m (ulp 2.4e-7), divided by delta = 0.2
+    np.testing.assert_allclose(out, np.clip((d32 - s) / delta, -1, 1), atol=1e-5)
+    np.testing.assert_allclose(out, -0.05, atol=1e-5)
 
 
 def test_visibility_rules():
@@ -127,7 +130,7 @@ def test_rigid_motion_invariance():
     same = np.isnan(f0) == np.isnan(f1)
     assert same.mean() > 0.99          # pixel choice may flip exactly on a pixel border
     ok = same & ~np.isnan(f0)
-    assert np.mean(np.abs(f0[ok] - f1[ok]) < 1e-9) > 0.99
+    assert np.mean(np.abs(f0[ok] - f1[ok]) < 1e-5) > 0.99
 
 
 def test_median_rule():
