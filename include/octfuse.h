@@ -1,0 +1,224 @@
+/*
+ * octfuse -- octree TV-L1 range-data fusion on one GB300 (sm_103a).
+ *
+ * C ABI of the library.  Every entry point takes plain pointers and sizes; no
+ * PyTorch or C++ type crosses it.  Pointers marked "host or device" may point
+ * to either (the library copies with cudaMemcpyDefault); pointers marked
+ * "device" must be device memory of the context's GPU.
+ *
+ * The method (Kehl et al., "An Octree-Based Approach towards Efficient
+ * Variational Range Data Fusion", BMVC 2016):
+ *   - Eq. 1 (Sec. 3.1): per frame i a truncated signed distance
+ *       f_i(x) = clamp((D_i(pi_i(x)) - ||x - C_i||) / delta, -1, 1)
+ *     and a binary weight w_i(x) (observed unless phi_i(x) < -eta);
+ *   - Eq. 2 (Sec. 3.1): top-down octree construction, a node splitting while
+ *     the spread max f - min f over it exceeds tau;
+ *   - Eq. 3-5 (Sec. 3.2): the fused field u* minimises
+ *       E(u) = integral of  sum_i w_i |u - f_i| / (sum_i w_i + gamma)
+ *                           + lambda |grad u|
+ *     over the leaves of an adaptive octree;
+ *   - Sec. 3.2 "Optimization on the Octree": leaves with |u| < tau_split are
+ *     split, subtrees whose leaves all hold |u| > tau_join with one sign are
+ *     joined.
+ * The minimiser here is the first-order primal-dual method the paper names as
+ * future work (Sec. 5, Chambolle & Pock), applied to the exact L1 energy.
+ *
+ * Data layout (all owned by the context, in HBM):
+ *   leaves sorted by Morton key of their minimum corner in finest-voxel units
+ *   (x bit k -> key bit 3k, y -> 3k+1, z -> 3k+2); level 0 = root,
+ *   max_depth = finest voxel; structure of arrays for key, level, u, ubar,
+ *   p_x, p_y, p_z, tau, sigma; per-leaf Eq. 1 samples as a sorted CSR.
+ *
+ * Streams: every call enqueues its work on the stream given at creation and
+ * is ordered with respect to earlier calls.  Calls that return host values
+ * (restructure, energy, export_*, num_leaves, solve) synchronise that stream.
+ *
+ * Errors: every call returns an ofu_status; ofu_last_error() describes the
+ * last failure.  OFU_EINVAL / OFU_ESTATE / OFU_ECAPACITY leave the context as
+ * it was.  OFU_ECUDA poisons the context: only ofu_destroy is valid after it.
+ * No call aborts the process or traps on the device.
+ */
+#ifndef OCTFUSE_H
+#define OCTFUSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ofu_ctx ofu_ctx;
+
+typedef enum {
+  OFU_OK = 0,
+  OFU_EINVAL = 1,      /* bad argument */
+  OFU_ENOMEM = 2,      /* device allocation failed */
+  OFU_ECUDA = 3,       /* CUDA error; context poisoned */
+  OFU_ESTATE = 4,      /* call not valid in the context's current state */
+  OFU_ECAPACITY = 5,   /* result would exceed max_leaves or a 32-bit index */
+  OFU_ETIMEOUT = 6     /* reserved: a bounded device wait gave up */
+} ofu_status;
+
+/* Solver and scene parameters.  Lengths in metres. */
+typedef struct {
+  double origin[3];    /* minimum corner of the cubic domain */
+  double extent;       /* edge length of the domain (> 0) */
+  int32_t max_depth;   /* D_max, 1..15: finest voxel = extent / 2^D_max */
+  int32_t sample_fp16; /* 0: Eq. 1 samples stored as float32, 1: as float16 */
+  double delta;        /* truncation band of Eq. 1 (> 0) */
+  double eta;          /* observation threshold of Sec. 3.1 (>= 0) */
+  double lambda;       /* TV weight of Eq. 3/5 (>= 0) */
+  double gamma;        /* normaliser offset of Eq. 5 (> 0) */
+  double tau_split;    /* split a leaf when |u| < tau_split */
+  double tau_join;     /* join a subtree when all |u| > tau_join (>= tau_split) */
+  double spread_tau;   /* Eq. 2 construction threshold (the paper uses 0.1) */
+  int64_t max_leaves;  /* hard cap on the leaf count (0 = 2^27, the maximum) */
+} ofu_params;
+
+/* Fills `p` with the defaults: origin (-0.5,-0.5,-0.5), extent 1, max_depth 6,
+ * float32 samples, delta 4 voxels, eta 2 delta, lambda 0.5, gamma 1e-3,
+ * tau_split 0.95, tau_join 0.99, spread_tau 0.1, max_leaves 0. */
+void ofu_default_params(ofu_params* p);
+
+/* Creates an empty context on the current CUDA device.  `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream), borrowed for the context's
+ * lifetime.  Device memory is allocated by the library (cudaMalloc) and
+ * released by ofu_destroy.  EINVAL for out-of-range parameters. */
+ofu_status ofu_create_octree(const ofu_params* params, void* cuda_stream, ofu_ctx** out);
+
+/* Releases everything the context owns.  NULL is ignored. */
+void ofu_destroy(ofu_ctx* ctx);
+
+/* Text of the last error of `ctx` (empty if none); valid until the next call
+ * on ctx.  With ctx == NULL, the last error of a failed ofu_create_octree. */
+const char* ofu_last_error(const ofu_ctx* ctx);
+
+/* Eq. 1-2, Sec. 3.1: takes F range frames and builds the initial octree.
+ *   depth: host or device, float32 [F][H][W], z-depth in metres along the
+ *          optical axis; 0, negative or NaN = invalid pixel (w = 0);
+ *          +inf = the ray saw no surface (f = +1, w = 1).
+ *   intr:  host or device, float64 [F][4] = fx, fy, cx, cy; pixel (px, py)
+ *          has its centre at (px + 0.5, py + 0.5).
+ *   pose:  host or device, float64 [F][16], camera-to-world 4x4 row-major,
+ *          camera axes x right, y down, z forward.
+ * The frames are copied into the context (re-integration after restructuring
+ * reads them).  Then: the median of the Eq. 1 samples at every finest-voxel
+ * centre (-1 where no frame observes it) is reduced top-down by Eq. 2 into
+ * the leaves; every leaf gets its sorted samples at its centre; face
+ * neighbours and step sizes are built; u = ubar = per-leaf median, p = 0.
+ * Replaces any earlier structure.  EINVAL for F, H, W < 1 or null pointers;
+ * ECAPACITY when leaves or samples exceed the caps. */
+ofu_status ofu_integrate_frames(ofu_ctx* ctx, int32_t F, int32_t H, int32_t W,
+                                const float* depth, const double* intr, const double* pose);
+
+/* n >= 0 primal-dual iterations on the current structure (Sec. 3.2 energy):
+ *   p    <- proj_{|p_l| <= lambda}(p + sigma_l grad ubar)
+ *   u'   <- clamp(prox of the L1 data term at u + tau_l div p, -1, 1)
+ *   ubar <- 2 u' - u,  u <- u'
+ * Asynchronous.  ESTATE before ofu_integrate_frames. */
+ofu_status ofu_iterate(ofu_ctx* ctx, int32_t n);
+
+/* Split/join pass (Sec. 3.2): leaves below max_depth with |u| < tau_split are
+ * replaced by all their finest descendants (children inherit u and p); every
+ * maximal subtree whose leaves all hold |u| > tau_join with one sign becomes
+ * one leaf holding the volume-weighted means of u and p.  New leaves get
+ * their Eq. 1 samples; neighbours and step sizes are rebuilt; ubar = u.
+ * Outputs (host pointers, each may be NULL): number of split leaves, of
+ * joined subtrees, and the new leaf count.  Synchronises the stream. */
+ofu_status ofu_restructure(ofu_ctx* ctx, int64_t* n_split, int64_t* n_join, int64_t* n_leaves);
+
+/* Energy of Eq. 5 (exact L1 terms) at the current u, the value of the dual
+ * problem at the current p, and their difference (the primal-dual gap, >= 0
+ * up to rounding), all accumulated in float64 in a fixed order.  Host
+ * pointers, each may be NULL.  Synchronises the stream. */
+ofu_status ofu_energy(ofu_ctx* ctx, double* primal, double* dual, double* gap);
+
+/* Current leaf count (host pointer). */
+ofu_status ofu_num_leaves(ofu_ctx* ctx, int64_t* n);
+
+/* Copies the leaves in key order: keys (uint64 Morton keys), levels (uint8)
+ * and u (float32).  Each destination is host or device and may be NULL;
+ * `cap` is the element capacity of each.  *n receives the leaf count;
+ * ECAPACITY (nothing copied) when cap < count.  Synchronises the stream. */
+ofu_status ofu_export_leaves(ofu_ctx* ctx, uint64_t* keys, uint8_t* levels, float* u,
+                             int64_t cap, int64_t* n);
+
+/* The whole hot path after ofu_integrate_frames: runs `iters` iterations in
+ * windows of `restructure_every` (0 = never restructure), restructuring after
+ * every window but the last; every `check_every` iterations (0 = never) it
+ * evaluates the energy and stops early once gap / max(|primal|, 1) < gap_tol.
+ * Outputs (host, may be NULL): iterations run, sum over iterations of the leaf
+ * count (leaf-iterations), and the final primal, dual, gap (energies3[3];
+ * evaluated once at the end when check_every = 0).  Synchronises. */
+ofu_status ofu_solve(ofu_ctx* ctx, int32_t iters, int32_t restructure_every, int32_t check_every,
+                     double gap_tol, int32_t* iters_done, int64_t* leaf_iters, double* energies3);
+
+/* ---- inspection and test hooks ----------------------------------------- */
+
+typedef enum {
+  OFU_FIELD_U = 0,          /* float32 [N] */
+  OFU_FIELD_UBAR = 1,       /* float32 [N] */
+  OFU_FIELD_P = 2,          /* float32 [3][N]: p_x then p_y then p_z */
+  OFU_FIELD_TAU = 3,        /* float32 [N] primal step sizes */
+  OFU_FIELD_SIGMA = 4,      /* float32 [N] dual step sizes */
+  OFU_FIELD_W = 5,          /* int32 [N] observed-sample counts */
+  OFU_FIELD_SAMPLE_OFF = 6, /* uint32 [N+1] CSR offsets of the samples */
+  OFU_FIELD_SAMPLES = 7     /* float32 [total]: sorted samples (float16 ones widened) */
+} ofu_field;
+
+/* Copies one per-leaf array to `dst` (host or device) holding `cap_items`
+ * elements of the field's type.  *n_items receives the element count;
+ * ECAPACITY (nothing copied) when cap_items is too small.  Synchronises. */
+ofu_status ofu_export_field(ofu_ctx* ctx, int32_t field, void* dst, int64_t cap_items,
+                            int64_t* n_items);
+
+/* Face-neighbour lists of one face (0..5 = +x, +y, +z, -x, -y, -z) as CSR:
+ * off int64 [N+1] and idx int64 [nnz] (host or device; either may be NULL to
+ * query nnz).  The neighbours across a face are the leaves containing a
+ * finest voxel that touches the face from outside, ascending in index; an
+ * empty list is the domain boundary.  ECAPACITY when cap < nnz. */
+ofu_status ofu_export_neighbours(ofu_ctx* ctx, int32_t face, int64_t* off, int64_t* idx,
+                                 int64_t cap, int64_t* nnz);
+
+/* Replaces the structure by n leaves given in ascending key order (keys
+ * uint64, levels uint8; host or device; they must tile the domain), takes
+ * their Eq. 1 samples from the stored frames and rebuilds neighbours and step
+ * sizes.  u (float32 [N]) and p (float32 [3][N]) are optional (NULL: u =
+ * median, p = 0); ubar = u.  ESTATE before ofu_integrate_frames, EINVAL when
+ * the leaves do not tile the domain. */
+ofu_status ofu_import_leaves(ofu_ctx* ctx, const uint64_t* keys, const uint8_t* levels, int64_t n,
+                             const float* u, const float* p);
+
+/* Overwrites u, ubar and p (float32 [N], [N], [3][N]; host or device; ubar
+ * may be NULL for ubar = u) on the current structure. */
+ofu_status ofu_set_state(ofu_ctx* ctx, const float* u, const float* ubar, const float* p, int64_t n);
+
+/* ---- measurement hooks --------------------------------------------------- */
+
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t ofu_kernel_launches(void);
+
+/* enable = 1 clears and starts per-launch timing of the two iteration kernels
+ * (dual step, primal step) with CUDA events recorded on the context's stream
+ * around each launch made by ofu_iterate / ofu_solve; enable = 0 stops it. */
+ofu_status ofu_profile(ofu_ctx* ctx, int32_t enable);
+
+/* Reads the timing since ofu_profile(ctx, 1) (synchronises): per kernel
+ * (index 0 = dual step, 1 = primal step) the summed device time in ms, the
+ * launch count, and the summed algorithmic bytes, i.e. every array element
+ * the kernel must read or write once per leaf (neighbour values re-read
+ * through the cache are not counted):
+ *   dual   45 B per leaf: ubar, level, three +face entries, p read and
+ *          written, sigma;
+ *   primal 57 B per leaf + each observed sample (4 B, or 2 B in float16):
+ *          u read and written, ubar written, level, six face entries, p,
+ *          tau, sample offset.
+ * Any output pointer may be NULL. */
+ofu_status ofu_profile_read(ofu_ctx* ctx, double* ms, int64_t* launches, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OCTFUSE_H */

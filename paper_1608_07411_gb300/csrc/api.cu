@@ -1,0 +1,731 @@
+// C ABI of octfuse: context management and the orchestration of the kernels
+// of build.cu / solve.cu on the caller's stream.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ofu_internal.cuh"
+
+namespace ofu {
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace ofu
+
+using namespace ofu;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// Persistent device buffers by role (content not kept across growth).
+enum Buf {
+  B_SCAN, B_U0, B_PYR, B_FLAGS, B_POS, B_CNT, B_OVFC, B_CLS, B_OUTC, B_JL, B_SRC, B_LIST,
+  B_SMALL, B_PART, B_NUM
+};
+
+struct Bufs {
+  void* p[B_NUM] = {};
+  size_t bytes[B_NUM] = {};
+};
+
+Bufs& bufs(ofu_ctx* c) {
+  // stored behind the scratch pointer of the context
+  return *reinterpret_cast<Bufs*>(c->scratch);
+}
+
+ofu_status fail(ofu_ctx* c, ofu_status st, const std::string& msg) {
+  c->err = msg;
+  return st;
+}
+
+ofu_status fail_cuda(ofu_ctx* c, cudaError_t e, const char* what) {
+  c->poisoned = true;
+  c->err = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? OFU_ENOMEM : OFU_ECUDA;
+}
+
+#define CU(call)                                                   \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return fail_cuda(ctx, e_, #call);       \
+  } while (0)
+
+#define ST(call)                                \
+  do {                                          \
+    ofu_status s_ = (call);                     \
+    if (s_ != OFU_OK) return s_;                \
+  } while (0)
+
+template <typename T>
+ofu_status ensure(ofu_ctx* ctx, Buf b, size_t count, T** out) {
+  Bufs& B = bufs(ctx);
+  const size_t need = std::max<size_t>(count * sizeof(T), 256);
+  if (B.bytes[b] < need) {
+    if (B.p[b]) CU(cudaFree(B.p[b]));
+    B.p[b] = nullptr;
+    B.bytes[b] = 0;
+    const size_t nb = need + need / 4;
+    CU(cudaMalloc(&B.p[b], nb));
+    B.bytes[b] = nb;
+  }
+  *out = reinterpret_cast<T*>(B.p[b]);
+  return OFU_OK;
+}
+
+void free_leaves(Leaves& L) {
+  cudaFree(L.key);
+  cudaFree(L.level);
+  cudaFree(L.u);
+  cudaFree(L.ubar);
+  cudaFree(L.p);
+  cudaFree(L.tau);
+  cudaFree(L.sigma);
+  cudaFree(L.nbr);
+  cudaFree(L.soff);
+  L = Leaves{};
+}
+
+ofu_status ensure_leaves(ofu_ctx* ctx, int which, int64_t need) {
+  Leaves& L = ctx->L[which];
+  if (L.cap >= need) return OFU_OK;
+  free_leaves(L);
+  const int64_t cap = std::max<int64_t>(need + need / 4, 1024);
+  CU(cudaMalloc(&L.key, cap * sizeof(uint64_t)));
+  CU(cudaMalloc(&L.level, cap));
+  CU(cudaMalloc(&L.u, cap * sizeof(float)));
+  CU(cudaMalloc(&L.ubar, cap * sizeof(float)));
+  CU(cudaMalloc(&L.p, 3 * cap * sizeof(float)));
+  CU(cudaMalloc(&L.tau, cap * sizeof(float)));
+  CU(cudaMalloc(&L.sigma, cap * sizeof(float)));
+  CU(cudaMalloc(&L.nbr, 6 * cap * sizeof(int32_t)));
+  CU(cudaMalloc(&L.soff, (cap + 1) * sizeof(uint32_t)));
+  L.cap = cap;
+  return OFU_OK;
+}
+
+size_t sample_bytes(const ofu_ctx* ctx) { return ctx->prm.sample_fp16 ? 2 : 4; }
+
+ofu_status ensure_samples(ofu_ctx* ctx, int which, int64_t need) {
+  if (ctx->samp_cap[which] >= need && ctx->samp[which]) return OFU_OK;
+  if (ctx->samp[which]) CU(cudaFree(ctx->samp[which]));
+  ctx->samp[which] = nullptr;
+  const int64_t cap = std::max<int64_t>(need + need / 4, 4096);
+  CU(cudaMalloc(&ctx->samp[which], size_t(cap) * sample_bytes(ctx) + 16));
+  ctx->samp_cap[which] = cap;
+  return OFU_OK;
+}
+
+View view_of(const ofu_ctx* ctx) {
+  const Leaves& L = ctx->L[ctx->cur];
+  View v;
+  v.n = ctx->n;
+  v.D = ctx->prm.max_depth;
+  v.key = L.key;
+  v.level = L.level;
+  v.nbr = L.nbr;
+  v.ovf = ctx->ovf;
+  v.stride = L.cap;
+  return v;
+}
+
+Geo geo_of(const ofu_ctx* ctx) {
+  Geo g;
+  for (int k = 0; k < 3; ++k) g.org[k] = float(ctx->prm.origin[k]);
+  g.vox = float(ctx->prm.extent) / float(1 << ctx->prm.max_depth);
+  g.delta = float(ctx->prm.delta);
+  g.eta = float(ctx->prm.eta);
+  g.D = ctx->prm.max_depth;
+  return g;
+}
+
+// Copies `bytes` from device to a pinned host staging area and waits.
+ofu_status read_back(ofu_ctx* ctx, const void* dev, size_t bytes, void* host) {
+  CU(cudaMemcpyAsync(ctx->pinned, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  std::memcpy(host, ctx->pinned, bytes);
+  return OFU_OK;
+}
+
+int64_t max_leaves(const ofu_ctx* ctx) {
+  return ctx->prm.max_leaves > 0 ? std::min<int64_t>(ctx->prm.max_leaves, kMaxLeaves) : kMaxLeaves;
+}
+
+// Face neighbours and step sizes of the current structure.
+ofu_status rebuild_topology(ofu_ctx* ctx) {
+  const int64_t n = ctx->n;
+  uint32_t* ovfc;
+  uint32_t* tmp;
+  ST(ensure(ctx, B_OVFC, size_t(6 * n + 1), &ovfc));
+  ST(ensure(ctx, B_SCAN, scan_tmp_items<uint32_t>(6 * n) * 2, &tmp));
+  View v = view_of(ctx);
+  CU(launch_nbr_count(v, ovfc, ctx->stream));
+  CU(scan_exclusive<uint32_t>(ovfc, ovfc, 6 * n, tmp, ctx->stream));
+  uint32_t total = 0;
+  ST(read_back(ctx, ovfc + 6 * n, sizeof(uint32_t), &total));
+  if (int64_t(total) + 1 > ctx->ovf_cap) {
+    if (ctx->ovf) CU(cudaFree(ctx->ovf));
+    ctx->ovf = nullptr;
+    const int64_t cap = std::max<int64_t>(int64_t(total) + int64_t(total) / 4 + 1, 1024);
+    if (cap >= 0x7fffffffLL) return fail(ctx, OFU_ECAPACITY, "neighbour lists exceed 2^31 entries");
+    CU(cudaMalloc(&ctx->ovf, size_t(cap) * sizeof(int32_t)));
+    ctx->ovf_cap = cap;
+  }
+  v = view_of(ctx);
+  Leaves& L = ctx->L[ctx->cur];
+  CU(launch_nbr_fill(v, ovfc, L.nbr, ctx->ovf, ctx->stream));
+  v = view_of(ctx);
+  CU(launch_precond(v, L.tau, L.sigma, ctx->stream));
+  return OFU_OK;
+}
+
+// Eq. 1 samples of all current leaves; with init, u = ubar = median, p = 0.
+ofu_status integrate_all(ofu_ctx* ctx, bool init) {
+  const int64_t n = ctx->n;
+  Leaves& L = ctx->L[ctx->cur];
+  const Geo g = geo_of(ctx);
+  uint32_t* tmp;
+  ST(ensure(ctx, B_SCAN, scan_tmp_items<uint32_t>(n) * 2, &tmp));
+  CU(launch_leaf_count(L.key, L.level, nullptr, n, ctx->depth, ctx->cams, ctx->F, ctx->H, ctx->W,
+                       g, L.soff, ctx->stream));
+  CU(scan_exclusive<uint32_t>(L.soff, L.soff, n, tmp, ctx->stream));
+  uint32_t total = 0;
+  ST(read_back(ctx, L.soff + n, sizeof(uint32_t), &total));
+  ST(ensure_samples(ctx, ctx->cur, int64_t(total)));
+  ctx->n_samples = total;
+  CU(launch_leaf_fill(L.key, L.level, nullptr, n, ctx->depth, ctx->cams, ctx->F, ctx->H, ctx->W,
+                      g, L.soff, ctx->samp[ctx->cur], ctx->prm.sample_fp16 != 0,
+                      init ? L.u : nullptr, init ? L.ubar : nullptr, ctx->stream));
+  if (init) CU(cudaMemsetAsync(L.p, 0, 3 * L.cap * sizeof(float), ctx->stream));
+  return OFU_OK;
+}
+
+// Count check on the sample total (offsets are 32-bit).
+bool samples_fit(int64_t n, int F) { return n * int64_t(F) < int64_t(0xffffffffu); }
+
+ofu_status check_ready(ofu_ctx* ctx) {
+  if (!ctx) return OFU_EINVAL;
+  if (ctx->poisoned) return fail(ctx, OFU_ESTATE, "context poisoned by an earlier CUDA error: " + ctx->err);
+  return OFU_OK;
+}
+
+ofu_status check_built(ofu_ctx* ctx) {
+  ST(check_ready(ctx));
+  if (!ctx->have_frames || ctx->n == 0) return fail(ctx, OFU_ESTATE, "no octree: call ofu_integrate_frames first");
+  return OFU_OK;
+}
+
+ofu_status validate(const ofu_params* p, std::string* why) {
+  auto bad = [&](const char* m) { *why = m; return OFU_EINVAL; };
+  if (!p) return bad("params is NULL");
+  if (!(p->extent > 0) || !std::isfinite(p->extent)) return bad("extent must be finite and > 0");
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(p->origin[k])) return bad("origin must be finite");
+  if (p->max_depth < 1 || p->max_depth > kMaxDepth) return bad("max_depth must be in 1..15");
+  if (!(p->delta > 0) || !std::isfinite(p->delta)) return bad("delta must be finite and > 0");
+  if (!(p->eta >= 0) || !std::isfinite(p->eta)) return bad("eta must be finite and >= 0");
+  if (!(p->lambda >= 0) || !std::isfinite(p->lambda)) return bad("lambda must be finite and >= 0");
+  if (!(p->gamma > 0) || !std::isfinite(p->gamma)) return bad("gamma must be finite and > 0");
+  if (std::isnan(p->tau_split) || std::isnan(p->tau_join) || std::isnan(p->spread_tau))
+    return bad("thresholds must not be NaN");
+  if (p->tau_join < p->tau_split) return bad("tau_join must be >= tau_split");
+  if (p->sample_fp16 != 0 && p->sample_fp16 != 1) return bad("sample_fp16 must be 0 or 1");
+  if (p->max_leaves < 0) return bad("max_leaves must be >= 0");
+  return OFU_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ofu_default_params(ofu_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  for (int k = 0; k < 3; ++k) p->origin[k] = -0.5;
+  p->extent = 1.0;
+  p->max_depth = 6;
+  p->sample_fp16 = 0;
+  p->delta = 4.0 / 64.0;
+  p->eta = 2.0 * p->delta;
+  p->lambda = 0.5;
+  p->gamma = 1e-3;
+  p->tau_split = 0.95;
+  p->tau_join = 0.99;
+  p->spread_tau = 0.1;
+  p->max_leaves = 0;
+}
+
+ofu_status ofu_create_octree(const ofu_params* params, void* cuda_stream, ofu_ctx** out) {
+  if (!out) {
+    g_create_error = "out is NULL";
+    return OFU_EINVAL;
+  }
+  *out = nullptr;
+  std::string why;
+  if (validate(params, &why) != OFU_OK) {
+    g_create_error = why;
+    return OFU_EINVAL;
+  }
+  ofu_ctx* ctx = new ofu_ctx();
+  ctx->prm = *params;
+  ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->pinned, 256);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("CUDA initialisation failed: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    delete ctx;
+    return e == cudaErrorMemoryAllocation ? OFU_ENOMEM : OFU_ECUDA;
+  }
+  ctx->scratch = new Bufs();
+  *out = ctx;
+  return OFU_OK;
+}
+
+void ofu_destroy(ofu_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  free_leaves(ctx->L[0]);
+  free_leaves(ctx->L[1]);
+  cudaFree(ctx->samp[0]);
+  cudaFree(ctx->samp[1]);
+  cudaFree(ctx->ovf);
+  cudaFree(ctx->depth);
+  cudaFree(ctx->cams);
+  if (ctx->scratch) {
+    Bufs& B = bufs(ctx);
+    for (int b = 0; b < B_NUM; ++b) cudaFree(B.p[b]);
+    delete &B;
+  }
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete ctx;
+}
+
+const char* ofu_last_error(const ofu_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+ofu_status ofu_integrate_frames(ofu_ctx* ctx, int32_t F, int32_t H, int32_t W, const float* depth,
+                                const double* intr, const double* pose) {
+  ST(check_ready(ctx));
+  if (F < 1 || H < 1 || W < 1 || !depth || !intr || !pose)
+    return fail(ctx, OFU_EINVAL, "integrate_frames: F, H, W must be >= 1 and pointers non-NULL");
+  if (F > 512) return fail(ctx, OFU_EINVAL, "integrate_frames: at most 512 frames");
+  if (int64_t(H) * W >= (int64_t(1) << 31)) return fail(ctx, OFU_EINVAL, "integrate_frames: frame too large");
+  const int D = ctx->prm.max_depth;
+  const int64_t nvox = int64_t(1) << (3 * D);
+  if (nvox >= (int64_t(1) << 32)) return fail(ctx, OFU_ECAPACITY, "max_depth too large for the dense construction pass");
+
+  // frames
+  std::vector<double> hi(size_t(F) * 4), hp(size_t(F) * 16);
+  CU(cudaMemcpy(hi.data(), intr, hi.size() * sizeof(double), cudaMemcpyDefault));
+  CU(cudaMemcpy(hp.data(), pose, hp.size() * sizeof(double), cudaMemcpyDefault));
+  std::vector<Cam> cams(F);
+  for (int i = 0; i < F; ++i) {
+    const double* P = &hp[size_t(i) * 16];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) cams[i].r[r * 3 + c] = float(P[r * 4 + c]);
+    for (int r = 0; r < 3; ++r) cams[i].c[r] = float(P[r * 4 + 3]);
+    cams[i].fx = float(hi[size_t(i) * 4 + 0]);
+    cams[i].fy = float(hi[size_t(i) * 4 + 1]);
+    cams[i].cx = float(hi[size_t(i) * 4 + 2]);
+    cams[i].cy = float(hi[size_t(i) * 4 + 3]);
+    if (!(cams[i].fx != 0.0f) || !(cams[i].fy != 0.0f))
+      return fail(ctx, OFU_EINVAL, "integrate_frames: focal lengths must be non-zero");
+  }
+  const size_t dbytes = size_t(F) * H * W * sizeof(float);
+  if (ctx->depth && size_t(ctx->F) * ctx->H * ctx->W * sizeof(float) < dbytes) {
+    CU(cudaFree(ctx->depth));
+    ctx->depth = nullptr;
+  }
+  if (!ctx->depth) CU(cudaMalloc(&ctx->depth, dbytes));
+  if (ctx->cams) CU(cudaFree(ctx->cams));
+  ctx->cams = nullptr;
+  CU(cudaMalloc(&ctx->cams, size_t(F) * sizeof(Cam)));
+  CU(cudaMemcpyAsync(ctx->depth, depth, dbytes, cudaMemcpyDefault, ctx->stream));
+  CU(cudaMemcpyAsync(ctx->cams, cams.data(), size_t(F) * sizeof(Cam), cudaMemcpyHostToDevice, ctx->stream));
+  ctx->F = F;
+  ctx->H = H;
+  ctx->W = W;
+  ctx->have_frames = true;
+  ctx->n = 0;
+
+  // Eq. 2 construction on the median field
+  const Geo g = geo_of(ctx);
+  double *u0, *pyr;
+  uint32_t *flags, *pos, *tmp;
+  ST(ensure(ctx, B_U0, size_t(nvox), &u0));
+  const int64_t npyr = ((int64_t(1) << (3 * D)) - 1) / 7;
+  ST(ensure(ctx, B_PYR, size_t(2 * npyr), &pyr));
+  ST(ensure(ctx, B_FLAGS, size_t(nvox), &flags));
+  ST(ensure(ctx, B_POS, size_t(nvox + 1), &pos));
+  ST(ensure(ctx, B_SCAN, scan_tmp_items<uint32_t>(nvox) * 2, &tmp));
+  CU(launch_dense_u0(ctx->depth, ctx->cams, F, H, W, g, u0, ctx->stream));
+  CU(launch_pyramid(u0, D, pyr, pyr + npyr, ctx->stream));
+  CU(launch_leaf_flags(pyr, pyr + npyr, D, ctx->prm.spread_tau, flags, ctx->stream));
+  CU(scan_exclusive<uint32_t>(flags, pos, nvox, tmp, ctx->stream));
+  uint32_t N = 0;
+  ST(read_back(ctx, pos + nvox, sizeof(uint32_t), &N));
+  if (int64_t(N) > max_leaves(ctx)) return fail(ctx, OFU_ECAPACITY, "construction exceeds max_leaves");
+  if (!samples_fit(N, F)) return fail(ctx, OFU_ECAPACITY, "sample count may exceed 2^32");
+  ST(ensure_leaves(ctx, ctx->cur, N));
+  Leaves& L = ctx->L[ctx->cur];
+  CU(launch_emit_constructed(flags, pos, pyr, pyr + npyr, D, ctx->prm.spread_tau, L.key, L.level,
+                             ctx->stream));
+  ctx->n = N;
+  ST(integrate_all(ctx, true));
+  ST(rebuild_topology(ctx));
+  return OFU_OK;
+}
+
+ofu_status ofu_iterate(ofu_ctx* ctx, int32_t n) {
+  ST(check_built(ctx));
+  if (n < 0) return fail(ctx, OFU_EINVAL, "iterate: n must be >= 0");
+  Leaves& L = ctx->L[ctx->cur];
+  const View v = view_of(ctx);
+  const bool h16 = ctx->prm.sample_fp16 != 0;
+  for (int k = 0; k < n; ++k) {
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    if (ctx->prof_on) {
+      while (ctx->prof_ev.size() < ctx->prof_used + 3) {
+        cudaEvent_t e;
+        CU(cudaEventCreate(&e));
+        ctx->prof_ev.push_back(e);
+      }
+      for (int j = 0; j < 3; ++j) ev[j] = ctx->prof_ev[ctx->prof_used + j];
+      ctx->prof_used += 3;
+      CU(cudaEventRecord(ev[0], ctx->stream));
+    }
+    CU(launch_dual(v, L.ubar, L.p, L.sigma, float(ctx->prm.lambda), ctx->stream));
+    if (ctx->prof_on) CU(cudaEventRecord(ev[1], ctx->stream));
+    CU(launch_primal(v, L.u, L.ubar, L.p, L.tau, L.soff, ctx->samp[ctx->cur], h16,
+                     float(ctx->prm.gamma), ctx->stream));
+    if (ctx->prof_on) {
+      CU(cudaEventRecord(ev[2], ctx->stream));
+      ctx->prof_launches[0] += 1;
+      ctx->prof_launches[1] += 1;
+      ctx->prof_bytes[0] += 45.0 * double(ctx->n);
+      ctx->prof_bytes[1] += 57.0 * double(ctx->n) + double(ctx->n_samples) * double(sample_bytes(ctx));
+    }
+  }
+  return OFU_OK;
+}
+
+ofu_status ofu_restructure(ofu_ctx* ctx, int64_t* n_split, int64_t* n_join, int64_t* n_leaves) {
+  ST(check_built(ctx));
+  const int64_t n = ctx->n;
+  const int D = ctx->prm.max_depth;
+  Leaves& L = ctx->L[ctx->cur];
+  uint64_t *cls, *outc, *tmp64, *small;
+  int8_t* jl;
+  ST(ensure(ctx, B_CLS, size_t(n + 1), &cls));
+  ST(ensure(ctx, B_OUTC, size_t(n + 1), &outc));
+  ST(ensure(ctx, B_JL, size_t(n), &jl));
+  ST(ensure(ctx, B_SCAN, scan_tmp_items<uint64_t>(n) * 2, &tmp64));
+  ST(ensure(ctx, B_SMALL, 8, &small));
+  View v = view_of(ctx);
+  CU(cudaMemsetAsync(small, 0, 8 * sizeof(uint64_t), ctx->stream));
+  CU(launch_classify(L.u, n, ctx->prm.tau_join, cls, ctx->stream));
+  CU(scan_exclusive<uint64_t>(cls, cls, n, tmp64, ctx->stream));
+  CU(launch_mark(v, L.u, cls, ctx->prm.tau_split, ctx->prm.tau_join, outc, jl,
+                 reinterpret_cast<unsigned long long*>(small), ctx->stream));
+  CU(scan_exclusive<uint64_t>(outc, outc, n, tmp64, ctx->stream));
+  CU(cudaMemcpyAsync(small + 2, outc + n, sizeof(uint64_t), cudaMemcpyDeviceToDevice, ctx->stream));
+  uint64_t hs[3];
+  ST(read_back(ctx, small, 3 * sizeof(uint64_t), hs));
+  const int64_t ns = int64_t(hs[0]), nj = int64_t(hs[1]), n_new = int64_t(hs[2]);
+  if (ns == 0 && nj == 0) {
+    CU(cudaMemcpyAsync(L.ubar, L.u, size_t(n) * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+    if (n_split) *n_split = 0;
+    if (n_join) *n_join = 0;
+    if (n_leaves) *n_leaves = n;
+    return OFU_OK;
+  }
+  if (n_new > max_leaves(ctx)) return fail(ctx, OFU_ECAPACITY, "restructure exceeds max_leaves");
+  if (!samples_fit(n_new, ctx->F)) return fail(ctx, OFU_ECAPACITY, "sample count may exceed 2^32");
+  const int nx = 1 - ctx->cur;
+  ST(ensure_leaves(ctx, nx, n_new));
+  Leaves& N2 = ctx->L[nx];
+  int32_t* src;
+  uint32_t *list, *tmp32;
+  ST(ensure(ctx, B_SRC, size_t(n_new), &src));
+  ST(ensure(ctx, B_LIST, size_t(n_new), &list));
+  ST(ensure(ctx, B_SCAN, std::max(scan_tmp_items<uint64_t>(n) * 2, scan_tmp_items<uint32_t>(n_new) * 2 / 2 + 1), &tmp64));
+  tmp32 = reinterpret_cast<uint32_t*>(tmp64);
+  v = view_of(ctx);
+  CU(launch_emit(v, L.u, L.p, outc, jl, n_new, N2.key, N2.level, N2.u, N2.ubar, N2.p, N2.cap, src,
+                 ctx->stream));
+  CU(cudaMemsetAsync(small + 3, 0, sizeof(uint64_t), ctx->stream));
+  CU(launch_new_list(src, n_new, list, reinterpret_cast<unsigned long long*>(small + 3), ctx->stream));
+  CU(launch_kept_counts(src, L.soff, n_new, N2.soff, ctx->stream));
+  uint64_t hl = 0;
+  ST(read_back(ctx, small + 3, sizeof(uint64_t), &hl));
+  const Geo g = geo_of(ctx);
+  CU(launch_leaf_count(N2.key, N2.level, list, int64_t(hl), ctx->depth, ctx->cams, ctx->F, ctx->H,
+                       ctx->W, g, N2.soff, ctx->stream));
+  CU(scan_exclusive<uint32_t>(N2.soff, N2.soff, n_new, tmp32, ctx->stream));
+  uint32_t total = 0;
+  ST(read_back(ctx, N2.soff + n_new, sizeof(uint32_t), &total));
+  ST(ensure_samples(ctx, nx, int64_t(total)));
+  const bool h16 = ctx->prm.sample_fp16 != 0;
+  CU(launch_copy_kept_samples(src, n_new, L.soff, ctx->samp[ctx->cur], N2.soff, ctx->samp[nx], h16,
+                              ctx->stream));
+  CU(launch_leaf_fill(N2.key, N2.level, list, int64_t(hl), ctx->depth, ctx->cams, ctx->F, ctx->H,
+                      ctx->W, g, N2.soff, ctx->samp[nx], h16, nullptr, nullptr, ctx->stream));
+  ctx->cur = nx;
+  ctx->n = n_new;
+  ctx->n_samples = total;
+  (void)D;
+  ST(rebuild_topology(ctx));
+  if (n_split) *n_split = ns;
+  if (n_join) *n_join = nj;
+  if (n_leaves) *n_leaves = n_new;
+  return OFU_OK;
+}
+
+ofu_status ofu_energy(ofu_ctx* ctx, double* primal, double* dual, double* gap) {
+  ST(check_built(ctx));
+  Leaves& L = ctx->L[ctx->cur];
+  double *part, *small;
+  ST(ensure(ctx, B_PART, energy_tmp_bytes(ctx->n) / sizeof(double) + 4, &part));
+  small = part + energy_tmp_bytes(ctx->n) / sizeof(double);
+  CU(launch_energy(view_of(ctx), L.u, L.p, L.soff, ctx->samp[ctx->cur], ctx->prm.sample_fp16 != 0,
+                   ctx->prm.lambda, ctx->prm.gamma, part, small, ctx->stream));
+  double h[3];
+  ST(read_back(ctx, small, 3 * sizeof(double), h));
+  if (primal) *primal = h[0];
+  if (dual) *dual = h[1];
+  if (gap) *gap = h[2];
+  return OFU_OK;
+}
+
+ofu_status ofu_num_leaves(ofu_ctx* ctx, int64_t* n) {
+  ST(check_ready(ctx));
+  if (!n) return fail(ctx, OFU_EINVAL, "num_leaves: n is NULL");
+  *n = ctx->n;
+  return OFU_OK;
+}
+
+ofu_status ofu_export_leaves(ofu_ctx* ctx, uint64_t* keys, uint8_t* levels, float* u, int64_t cap,
+                             int64_t* n) {
+  ST(check_ready(ctx));
+  if (n) *n = ctx->n;
+  if ((keys || levels || u) && cap < ctx->n)
+    return fail(ctx, OFU_ECAPACITY, "export_leaves: capacity smaller than the leaf count");
+  Leaves& L = ctx->L[ctx->cur];
+  const size_t m = size_t(ctx->n);
+  if (m) {
+    if (keys) CU(cudaMemcpyAsync(keys, L.key, m * sizeof(uint64_t), cudaMemcpyDefault, ctx->stream));
+    if (levels) CU(cudaMemcpyAsync(levels, L.level, m, cudaMemcpyDefault, ctx->stream));
+    if (u) CU(cudaMemcpyAsync(u, L.u, m * sizeof(float), cudaMemcpyDefault, ctx->stream));
+  }
+  CU(cudaStreamSynchronize(ctx->stream));
+  return OFU_OK;
+}
+
+ofu_status ofu_solve(ofu_ctx* ctx, int32_t iters, int32_t restructure_every, int32_t check_every,
+                     double gap_tol, int32_t* iters_done, int64_t* leaf_iters, double* energies3) {
+  ST(check_built(ctx));
+  if (iters < 0 || restructure_every < 0 || check_every < 0)
+    return fail(ctx, OFU_EINVAL, "solve: counts must be >= 0");
+  int32_t done = 0;
+  int64_t li = 0;
+  double e[3] = {0.0, 0.0, 0.0};
+  bool have_e = false;
+  while (done < iters) {
+    int32_t step = iters - done;
+    if (restructure_every > 0) step = std::min(step, restructure_every);
+    if (check_every > 0) step = std::min(step, check_every - (done % check_every));
+    ST(ofu_iterate(ctx, step));
+    li += int64_t(step) * ctx->n;
+    done += step;
+    have_e = false;
+    if (check_every > 0 && done % check_every == 0) {
+      ST(ofu_energy(ctx, &e[0], &e[1], &e[2]));
+      have_e = true;
+      if (gap_tol > 0 && e[2] / std::max(std::fabs(e[0]), 1.0) < gap_tol) break;
+    }
+    if (restructure_every > 0 && done % restructure_every == 0 && done < iters) {
+      ST(ofu_restructure(ctx, nullptr, nullptr, nullptr));
+      have_e = false;
+    }
+  }
+  if (energies3) {
+    if (!have_e) ST(ofu_energy(ctx, &e[0], &e[1], &e[2]));
+    for (int k = 0; k < 3; ++k) energies3[k] = e[k];
+  } else {
+    CU(cudaStreamSynchronize(ctx->stream));
+  }
+  if (iters_done) *iters_done = done;
+  if (leaf_iters) *leaf_iters = li;
+  return OFU_OK;
+}
+
+ofu_status ofu_export_field(ofu_ctx* ctx, int32_t field, void* dst, int64_t cap_items,
+                            int64_t* n_items) {
+  ST(check_ready(ctx));
+  const int64_t n = ctx->n;
+  Leaves& L = ctx->L[ctx->cur];
+  int64_t items;
+  switch (field) {
+    case OFU_FIELD_U: case OFU_FIELD_UBAR: case OFU_FIELD_TAU: case OFU_FIELD_SIGMA: case OFU_FIELD_W:
+      items = n; break;
+    case OFU_FIELD_P: items = 3 * n; break;
+    case OFU_FIELD_SAMPLE_OFF: items = n + 1; break;
+    case OFU_FIELD_SAMPLES: items = ctx->n_samples; break;
+    default: return fail(ctx, OFU_EINVAL, "export_field: unknown field");
+  }
+  if (n_items) *n_items = items;
+  if (!dst) return OFU_OK;
+  if (cap_items < items) return fail(ctx, OFU_ECAPACITY, "export_field: capacity too small");
+  if (n == 0) return OFU_OK;
+  cudaStream_t s = ctx->stream;
+  switch (field) {
+    case OFU_FIELD_U: CU(cudaMemcpyAsync(dst, L.u, n * 4, cudaMemcpyDefault, s)); break;
+    case OFU_FIELD_UBAR: CU(cudaMemcpyAsync(dst, L.ubar, n * 4, cudaMemcpyDefault, s)); break;
+    case OFU_FIELD_TAU: CU(cudaMemcpyAsync(dst, L.tau, n * 4, cudaMemcpyDefault, s)); break;
+    case OFU_FIELD_SIGMA: CU(cudaMemcpyAsync(dst, L.sigma, n * 4, cudaMemcpyDefault, s)); break;
+    case OFU_FIELD_P:
+      for (int d = 0; d < 3; ++d)
+        CU(cudaMemcpyAsync(reinterpret_cast<float*>(dst) + d * n, L.p + d * L.cap, n * 4, cudaMemcpyDefault, s));
+      break;
+    case OFU_FIELD_SAMPLE_OFF: CU(cudaMemcpyAsync(dst, L.soff, (n + 1) * 4, cudaMemcpyDefault, s)); break;
+    case OFU_FIELD_W: {
+      int32_t* w;
+      ST(ensure(ctx, B_CNT, size_t(n), &w));
+      CU(launch_w_from_soff(L.soff, n, w, s));
+      CU(cudaMemcpyAsync(dst, w, n * 4, cudaMemcpyDefault, s));
+      break;
+    }
+    case OFU_FIELD_SAMPLES: {
+      float* w;
+      ST(ensure(ctx, B_CNT, size_t(items), &w));
+      CU(launch_widen_samples(ctx->samp[ctx->cur], ctx->prm.sample_fp16 != 0, items, w, s));
+      CU(cudaMemcpyAsync(dst, w, items * 4, cudaMemcpyDefault, s));
+      break;
+    }
+  }
+  CU(cudaStreamSynchronize(s));
+  return OFU_OK;
+}
+
+ofu_status ofu_export_neighbours(ofu_ctx* ctx, int32_t face, int64_t* off, int64_t* idx, int64_t cap,
+                                 int64_t* nnz) {
+  ST(check_built(ctx));
+  if (face < 0 || face > 5) return fail(ctx, OFU_EINVAL, "export_neighbours: face must be 0..5");
+  const int64_t n = ctx->n;
+  Leaves& L = ctx->L[ctx->cur];
+  std::vector<int32_t> e(n);
+  CU(cudaMemcpyAsync(e.data(), L.nbr + int64_t(face) * L.cap, n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  std::vector<int32_t> ov(ctx->ovf_cap > 0 ? size_t(ctx->ovf_cap) : 0);
+  if (!ov.empty()) CU(cudaMemcpyAsync(ov.data(), ctx->ovf, ov.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  std::vector<int64_t> ho(n + 1), hx;
+  ho[0] = 0;
+  for (int64_t l = 0; l < n; ++l) {
+    const int32_t x = e[l];
+    if (x == kEmpty) {
+    } else if (x >= 0) {
+      hx.push_back(entry_idx(x));
+    } else {
+      const uint32_t st = list_start(x);
+      for (int32_t k = 0; k < ov[st]; ++k) hx.push_back(entry_idx(ov[st + 1 + k]));
+    }
+    ho[l + 1] = int64_t(hx.size());
+  }
+  if (nnz) *nnz = int64_t(hx.size());
+  if (idx && cap < int64_t(hx.size())) return fail(ctx, OFU_ECAPACITY, "export_neighbours: capacity too small");
+  if (off) CU(cudaMemcpy(off, ho.data(), ho.size() * 8, cudaMemcpyDefault));
+  if (idx && !hx.empty()) CU(cudaMemcpy(idx, hx.data(), hx.size() * 8, cudaMemcpyDefault));
+  return OFU_OK;
+}
+
+ofu_status ofu_import_leaves(ofu_ctx* ctx, const uint64_t* keys, const uint8_t* levels, int64_t n,
+                             const float* u, const float* p) {
+  ST(check_ready(ctx));
+  if (!ctx->have_frames) return fail(ctx, OFU_ESTATE, "import_leaves: call ofu_integrate_frames first");
+  if (n < 1 || !keys || !levels) return fail(ctx, OFU_EINVAL, "import_leaves: need n >= 1 leaves");
+  if (n > max_leaves(ctx)) return fail(ctx, OFU_ECAPACITY, "import_leaves: more than max_leaves");
+  if (!samples_fit(n, ctx->F)) return fail(ctx, OFU_ECAPACITY, "sample count may exceed 2^32");
+  // stage into the spare buffer, check, then make it current
+  const int nx = 1 - ctx->cur;
+  ST(ensure_leaves(ctx, nx, n));
+  Leaves& L = ctx->L[nx];
+  CU(cudaMemcpyAsync(L.key, keys, n * 8, cudaMemcpyDefault, ctx->stream));
+  CU(cudaMemcpyAsync(L.level, levels, n, cudaMemcpyDefault, ctx->stream));
+  uint32_t* bad;
+  ST(ensure(ctx, B_CNT, 1, &bad));
+  CU(cudaMemsetAsync(bad, 0, 4, ctx->stream));
+  CU(launch_check_tiling(L.key, L.level, n, ctx->prm.max_depth, bad, ctx->stream));
+  uint32_t hb = 0;
+  ST(read_back(ctx, bad, 4, &hb));
+  if (hb) return fail(ctx, OFU_EINVAL, "import_leaves: leaves do not tile the domain in key order");
+  ctx->cur = nx;
+  ctx->n = n;
+  ST(integrate_all(ctx, true));
+  if (u) {
+    CU(cudaMemcpyAsync(L.u, u, n * 4, cudaMemcpyDefault, ctx->stream));
+    CU(cudaMemcpyAsync(L.ubar, u, n * 4, cudaMemcpyDefault, ctx->stream));
+  }
+  if (p) {
+    for (int d = 0; d < 3; ++d)
+      CU(cudaMemcpyAsync(L.p + d * L.cap, p + d * n, n * 4, cudaMemcpyDefault, ctx->stream));
+  }
+  ST(rebuild_topology(ctx));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return OFU_OK;
+}
+
+ofu_status ofu_set_state(ofu_ctx* ctx, const float* u, const float* ubar, const float* p, int64_t n) {
+  ST(check_built(ctx));
+  if (n != ctx->n || !u || !p) return fail(ctx, OFU_EINVAL, "set_state: n must equal the leaf count; u and p required");
+  Leaves& L = ctx->L[ctx->cur];
+  CU(cudaMemcpyAsync(L.u, u, n * 4, cudaMemcpyDefault, ctx->stream));
+  CU(cudaMemcpyAsync(L.ubar, ubar ? ubar : u, n * 4, cudaMemcpyDefault, ctx->stream));
+  for (int d = 0; d < 3; ++d)
+    CU(cudaMemcpyAsync(L.p + d * L.cap, p + d * n, n * 4, cudaMemcpyDefault, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return OFU_OK;
+}
+
+int64_t ofu_kernel_launches(void) { return launches_so_far(); }
+
+ofu_status ofu_profile(ofu_ctx* ctx, int32_t enable) {
+  ST(check_ready(ctx));
+  ctx->prof_on = enable != 0;
+  if (enable) {
+    ctx->prof_used = 0;
+    ctx->prof_bytes[0] = ctx->prof_bytes[1] = 0.0;
+    ctx->prof_launches[0] = ctx->prof_launches[1] = 0;
+  }
+  return OFU_OK;
+}
+
+ofu_status ofu_profile_read(ofu_ctx* ctx, double* ms, int64_t* launches, double* bytes) {
+  ST(check_ready(ctx));
+  CU(cudaStreamSynchronize(ctx->stream));
+  double t[2] = {0.0, 0.0};
+  for (size_t i = 0; i + 3 <= ctx->prof_used; i += 3) {
+    float a = 0.0f, b = 0.0f;
+    CU(cudaEventElapsedTime(&a, ctx->prof_ev[i], ctx->prof_ev[i + 1]));
+    CU(cudaEventElapsedTime(&b, ctx->prof_ev[i + 1], ctx->prof_ev[i + 2]));
+    t[0] += a;
+    t[1] += b;
+  }
+  for (int k = 0; k < 2; ++k) {
+    if (ms) ms[k] = t[k];
+    if (launches) launches[k] = ctx->prof_launches[k];
+    if (bytes) bytes[k] = ctx->prof_bytes[k];
+  }
+  return OFU_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,266 @@
+// Internal declarations of the octfuse CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/octfuse.h"
+
+namespace ofu {
+
+// ---------------------------------------------------------------------------
+// Face-neighbour entries.  Each leaf has one int32 entry per face:
+//   kEmpty (-1)                     domain boundary
+//   bit31 = 0                       one neighbour of the same or a coarser
+//                                   level: bits 0..26 index, 27..30 level
+//   bit31 = 1, not kEmpty           list of finer neighbours starting at
+//                                   ovf[bits 0..30]: ovf[start] = count,
+//                                   then count entries (index | level << 27)
+// so the common case costs one 4-byte read and carries the neighbour's level.
+constexpr int32_t kEmpty = -1;
+constexpr uint32_t kIdxMask = (1u << 27) - 1;
+constexpr int kMaxDepth = 15;
+constexpr int64_t kMaxLeaves = int64_t(1) << 27;
+
+__host__ __device__ inline int32_t make_single(uint32_t idx, int level) {
+  return int32_t(idx | (uint32_t(level) << 27));
+}
+__host__ __device__ inline int32_t make_list(uint32_t start) { return int32_t(0x80000000u | start); }
+__host__ __device__ inline bool is_single(int32_t e) { return e >= 0; }
+__host__ __device__ inline bool is_list(int32_t e) { return e < 0 && e != kEmpty; }
+__host__ __device__ inline uint32_t entry_idx(int32_t e) { return uint32_t(e) & kIdxMask; }
+__host__ __device__ inline int entry_level(int32_t e) { return int((uint32_t(e) >> 27) & 15u); }
+__host__ __device__ inline uint32_t list_start(int32_t e) { return uint32_t(e) & 0x7fffffffu; }
+
+// ---------------------------------------------------------------------------
+// Morton keys: bit k of x -> bit 3k, y -> 3k+1, z -> 3k+2.
+
+__host__ __device__ inline uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x1fffffu;
+  x = (x | x << 32) & 0x1f00000000ffffull;
+  x = (x | x << 16) & 0x1f0000ff0000ffull;
+  x = (x | x << 8) & 0x100f00f00f00f00full;
+  x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+  x = (x | x << 2) & 0x1249249249249249ull;
+  return x;
+}
+__host__ __device__ inline uint32_t compact3(uint64_t x) {
+  x &= 0x1249249249249249ull;
+  x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+  x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+  x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+  x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+  x = (x ^ (x >> 32)) & 0x1fffffull;
+  return uint32_t(x);
+}
+__host__ __device__ inline uint64_t morton(uint32_t x, uint32_t y, uint32_t z) {
+  return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+
+// ---------------------------------------------------------------------------
+// One frame's camera in float32 (Eq. 1 is evaluated in float32).
+struct Cam {
+  float r[9];  // camera-to-world rotation, row-major
+  float c[3];  // centre C_i
+  float fx, fy, cx, cy;
+};
+
+// Geometry shared by the Eq. 1 kernels.
+struct Geo {
+  float org[3];  // domain minimum corner
+  float vox;     // finest voxel edge = extent / 2^D
+  float delta, eta;
+  int D;
+};
+
+// Eq. 1 for one point and one frame, float32 with one rounding per
+// operation in a fixed order (no contraction into fused multiply-adds).
+// Returns false when the frame does not observe the point (w = 0).
+__device__ __forceinline__ bool eq1_sample(const Cam& k, const float* __restrict__ depth, int H,
+                                           int W, float x, float y, float z, float delta, float eta,
+                                           float* f) {
+  const float dx = __fsub_rn(x, k.c[0]);
+  const float dy = __fsub_rn(y, k.c[1]);
+  const float dz = __fsub_rn(z, k.c[2]);
+  const float xc = __fadd_rn(__fadd_rn(__fmul_rn(k.r[0], dx), __fmul_rn(k.r[3], dy)), __fmul_rn(k.r[6], dz));
+  const float yc = __fadd_rn(__fadd_rn(__fmul_rn(k.r[1], dx), __fmul_rn(k.r[4], dy)), __fmul_rn(k.r[7], dz));
+  const float zc = __fadd_rn(__fadd_rn(__fmul_rn(k.r[2], dx), __fmul_rn(k.r[5], dy)), __fmul_rn(k.r[8], dz));
+  if (!(zc > 0.0f)) return false;
+  const float u = __fadd_rn(__fmul_rn(k.fx, __fdiv_rn(xc, zc)), k.cx);
+  const float v = __fadd_rn(__fmul_rn(k.fy, __fdiv_rn(yc, zc)), k.cy);
+  if (!(u >= 0.0f && u < float(W) && v >= 0.0f && v < float(H))) return false;
+  const int px = int(floorf(u));
+  const int py = int(floorf(v));
+  const float d = __ldg(depth + size_t(py) * W + px);
+  if (!(d > 0.0f)) return false;
+  const float a = __fdiv_rn(__fsub_rn(__fadd_rn(float(px), 0.5f), k.cx), k.fx);
+  const float b = __fdiv_rn(__fsub_rn(__fadd_rn(float(py), 0.5f), k.cy), k.fy);
+  const float rl = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)), 1.0f));
+  const float rng = __fmul_rn(d, rl);
+  const float dist = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)));
+  const float phi = __fsub_rn(rng, dist);
+  if (!(phi >= -eta)) return false;
+  *f = fminf(fmaxf(__fdiv_rn(phi, delta), -1.0f), 1.0f);
+  return true;
+}
+
+// Leaf centre in float32: origin + (corner + h/2) * voxel.
+__device__ __forceinline__ float centre_coord(float org, uint32_t corner, uint32_t h, float vox) {
+  const float mid = __fadd_rn(float(corner), __fmul_rn(0.5f, float(h)));
+  return __fadd_rn(org, __fmul_rn(mid, vox));
+}
+
+// ---------------------------------------------------------------------------
+// Device buffers of one copy of the leaf arrays.
+struct Leaves {
+  int64_t cap = 0;
+  uint64_t* key = nullptr;
+  uint8_t* level = nullptr;
+  float* u = nullptr;
+  float* ubar = nullptr;
+  float* p = nullptr;      // [3][cap]
+  float* tau = nullptr;
+  float* sigma = nullptr;
+  int32_t* nbr = nullptr;  // [6][cap]
+  uint32_t* soff = nullptr;  // [cap + 1]
+};
+
+// Raw view of the current structure handed to kernels.
+struct View {
+  int64_t n;
+  int D;
+  const uint64_t* key;
+  const uint8_t* level;
+  const int32_t* nbr;  // [6][stride]
+  const int32_t* ovf;
+  int64_t stride;      // leaf capacity (row pitch of nbr and p)
+};
+
+}  // namespace ofu
+
+// ---------------------------------------------------------------------------
+// The context (opaque to callers).
+struct ofu_ctx {
+  ofu_params prm{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+  bool poisoned = false;
+
+  // frames (copied in by ofu_integrate_frames)
+  int F = 0, H = 0, W = 0;
+  float* depth = nullptr;
+  ofu::Cam* cams = nullptr;
+  bool have_frames = false;
+
+  // leaves: two copies, swapped by restructuring
+  ofu::Leaves L[2];
+  int cur = 0;
+  int64_t n = 0;
+
+  // samples (sorted CSR), double buffered like the leaves
+  void* samp[2] = {nullptr, nullptr};
+  int64_t samp_cap[2] = {0, 0};
+  int64_t n_samples = 0;
+
+  // overflow lists of finer face neighbours
+  int32_t* ovf = nullptr;
+  int64_t ovf_cap = 0;
+
+  // scratch (grown on demand)
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  void* pinned = nullptr;  // small host staging for scalar results
+
+  // per-launch timing of the iteration kernels (ofu_profile)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;   // pool, 3 per iteration
+  size_t prof_used = 0;
+  double prof_bytes[2] = {0.0, 0.0};
+  int64_t prof_launches[2] = {0, 0};
+};
+
+namespace ofu {
+
+// Process-wide count of kernel launches made by this library.
+void count_launches(int64_t k);
+int64_t launches_so_far();
+
+// ---------------------------------------------------------------------------
+// Launchers (defined in build.cu / solve.cu).  All enqueue on `s`.
+
+// Exclusive prefix sum of n items into out[0..n] (out[n] = total).  `in`
+// and `out` may alias.  `tmp` needs scan_tmp_items<T>(n) elements.
+template <typename T>
+size_t scan_tmp_items(int64_t n);
+template <typename T>
+cudaError_t scan_exclusive(const T* in, T* out, int64_t n, T* tmp, cudaStream_t s);
+
+// Median field at finest-voxel centres (Morton order), then the Eq. 2 min/max
+// pyramid and the per-voxel leaf flags.
+cudaError_t launch_dense_u0(const float* depth, const Cam* cams, int F, int H, int W, Geo g,
+                            double* u0, cudaStream_t s);
+cudaError_t launch_pyramid(const double* u0, int D, double* mn, double* mx, cudaStream_t s);
+cudaError_t launch_leaf_flags(const double* mn, const double* mx, int D, double spread_tau,
+                              uint32_t* flags, cudaStream_t s);
+cudaError_t launch_emit_constructed(const uint32_t* flags, const uint32_t* pos,
+                                    const double* mn, const double* mx, int D, double spread_tau,
+                                    uint64_t* key, uint8_t* level, cudaStream_t s);
+
+// Eq. 1 samples of leaves: counts (W) and the sorted CSR fill.  `list` selects
+// leaves (nullptr = all n).  fill also writes u = ubar = median when init.
+cudaError_t launch_leaf_count(const uint64_t* key, const uint8_t* level, const uint32_t* list,
+                              int64_t n, const float* depth, const Cam* cams, int F, int H, int W,
+                              Geo g, uint32_t* count, cudaStream_t s);
+cudaError_t launch_leaf_fill(const uint64_t* key, const uint8_t* level, const uint32_t* list,
+                             int64_t n, const float* depth, const Cam* cams, int F, int H, int W,
+                             Geo g, const uint32_t* soff, void* samp, bool fp16, float* u,
+                             float* ubar, cudaStream_t s);
+
+// Face neighbours (two passes) and step sizes.
+cudaError_t launch_nbr_count(View v, uint32_t* ovf_count, cudaStream_t s);
+cudaError_t launch_nbr_fill(View v, const uint32_t* ovf_off, int32_t* nbr, int32_t* ovf,
+                            cudaStream_t s);
+cudaError_t launch_precond(View v, float* tau, float* sigma, cudaStream_t s);
+cudaError_t launch_check_tiling(const uint64_t* key, const uint8_t* level, int64_t n, int D,
+                                uint32_t* bad, cudaStream_t s);
+
+// Restructuring.
+cudaError_t launch_classify(const float* u, int64_t n, double tau_j, uint64_t* cls,
+                            cudaStream_t s);
+cudaError_t launch_mark(View v, const float* u, const uint64_t* cls_scan, double tau_s,
+                        double tau_j, uint64_t* out_count, int8_t* join_level,
+                        unsigned long long* counters, cudaStream_t s);
+cudaError_t launch_emit(View v, const float* u, const float* p, const uint64_t* out_off,
+                        const int8_t* join_level, int64_t n_new, uint64_t* nkey, uint8_t* nlevel,
+                        float* nu, float* nubar, float* np_, int64_t nstride, int32_t* src,
+                        cudaStream_t s);
+cudaError_t launch_new_list(const int32_t* src, int64_t n, uint32_t* list,
+                            unsigned long long* cnt, cudaStream_t s);
+cudaError_t launch_kept_counts(const int32_t* src, const uint32_t* old_soff, int64_t n,
+                               uint32_t* count, cudaStream_t s);
+cudaError_t launch_copy_kept_samples(const int32_t* src, int64_t n, const uint32_t* old_soff,
+                                     const void* old_samp, const uint32_t* new_soff,
+                                     void* new_samp, bool fp16, cudaStream_t s);
+
+// Solver kernels.
+cudaError_t launch_dual(View v, const float* ubar, float* p, const float* sigma, float lambda,
+                        cudaStream_t s);
+cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const float* tau,
+                          const uint32_t* soff, const void* samp, bool fp16, float gamma,
+                          cudaStream_t s);
+size_t energy_tmp_bytes(int64_t n);
+cudaError_t launch_energy(View v, const float* u, const float* p, const uint32_t* soff,
+                          const void* samp, bool fp16, double lambda, double gamma,
+                          double* partial, double* out3, cudaStream_t s);
+
+// Export helpers.
+cudaError_t launch_widen_samples(const void* samp, bool fp16, int64_t n, float* out,
+                                 cudaStream_t s);
+cudaError_t launch_w_from_soff(const uint32_t* soff, int64_t n, int32_t* out, cudaStream_t s);
+
+}  // namespace ofu
