@@ -194,6 +194,32 @@ ofu_status ofu_import_leaves(ofu_ctx* ctx, const uint64_t* keys, const uint8_t* 
  * may be NULL for ubar = u) on the current structure. */
 ofu_status ofu_set_state(ofu_ctx* ctx, const float* u, const float* ubar, const float* p, int64_t n);
 
+/* ---- allocation-free variant -------------------------------------------- */
+
+/* ofu_energy for callers that must not cause a device allocation: a caller
+ * whose GPU memory is already owned by another allocator (a framework's
+ * caching allocator that has reserved the device, a fixed memory budget), or
+ * a latency-critical loop that forbids cudaMalloc / cudaFree, which
+ * synchronise the device, once it is running.  ofu_energy may allocate its
+ * reduction buffer on first use; this variant allocates nothing.  The paper
+ * has no counterpart: this is an interface convenience, the arithmetic is
+ * that of ofu_energy (same per-leaf float64 terms, partials summed in a fixed
+ * order, so results agree to rounding).
+ *
+ * Input: the context's current iterate.  Output: out3[3] = primal energy,
+ * dual value, gap; host or device memory.  Synchronises the stream.
+ *
+ * Scratch: a file-scope device array of 8192 x 2 + 3 doubles (about 128 KiB),
+ * present on every GPU that loads the library until the process exits.  One
+ * partial pair per block of 2048 leaves, so at most 16,777,216 leaves:
+ * larger octrees get OFU_ECAPACITY with a message naming the limit.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the array and each overwrites it, so calls that overlap on
+ * the GPU (several streams or threads at once) race and must be serialised
+ * by the caller. */
+ofu_status ofu_energy_static(ofu_ctx* ctx, double* out3);
+
 /* ---- measurement hooks --------------------------------------------------- */
 
 /* Number of CUDA kernels this library has launched in this process. */

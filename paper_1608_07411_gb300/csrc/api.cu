@@ -696,6 +696,25 @@ ofu_status ofu_set_state(ofu_ctx* ctx, const float* u, const float* ubar, const 
   return OFU_OK;
 }
 
+ofu_status ofu_energy_static(ofu_ctx* ctx, double* out3) {
+  ST(check_built(ctx));
+  if (!out3) return fail(ctx, OFU_EINVAL, "energy_static: out3 is NULL");
+  if (ctx->n > energy_static_max_leaves())
+    return fail(ctx, OFU_ECAPACITY, "energy_static: " + std::to_string(ctx->n) +
+                                        " leaves exceed its fixed scratch limit of " +
+                                        std::to_string(energy_static_max_leaves()) + " leaves");
+  double* scratch = nullptr;
+  CU(energy_static_scratch(&scratch));
+  Leaves& L = ctx->L[ctx->cur];
+  CU(launch_energy_static(view_of(ctx), L.u, L.p, L.soff, ctx->samp[ctx->cur],
+                          ctx->prm.sample_fp16 != 0, ctx->prm.lambda, ctx->prm.gamma, scratch,
+                          ctx->stream));
+  CU(cudaMemcpyAsync(out3, scratch + energy_static_result_offset(), 3 * sizeof(double),
+                     cudaMemcpyDefault, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return OFU_OK;
+}
+
 int64_t ofu_kernel_launches(void) { return launches_so_far(); }
 
 ofu_status ofu_profile(ofu_ctx* ctx, int32_t enable) {

@@ -258,6 +258,14 @@ cudaError_t launch_energy(View v, const float* u, const float* p, const uint32_t
                           const void* samp, bool fp16, double lambda, double gamma,
                           double* partial, double* out3, cudaStream_t s);
 
+// Energy with its scratch in a file-scope device array (solve.cu).
+int64_t energy_static_max_leaves();
+cudaError_t energy_static_scratch(double** ptr);
+cudaError_t launch_energy_static(View v, const float* u, const float* p, const uint32_t* soff,
+                                 const void* samp, bool fp16, double lambda, double gamma,
+                                 double* scratch, cudaStream_t s);
+int energy_static_result_offset();
+
 // Export helpers.
 cudaError_t launch_widen_samples(const void* samp, bool fp16, int64_t n, float* out,
                                  cudaStream_t s);

@@ -10,6 +10,8 @@
 // divergence gathers from the -face lists and nothing is scattered.
 #include <math_constants.h>
 
+#include <mutex>
+
 #include "ofu_internal.cuh"
 
 namespace ofu {
@@ -314,5 +316,62 @@ cudaError_t launch_energy(View v, const float* u, const float* p, const uint32_t
   count_launches(1);
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Energy without allocation: the same per-leaf energy kernel, its block
+// partials and the three results kept in a file-scope device array instead of
+// context memory.  Each block covers up to kStaticLeavesPerBlock leaves, so
+// the array bounds the leaf count.
+
+namespace {
+constexpr int kStaticEnergyBlocks = 8192;
+constexpr int64_t kStaticLeavesPerBlock = int64_t(kThreads) * 8;
+}  // namespace
+
+// [2 * kStaticEnergyBlocks] block partials, then [3] primal, dual, gap.
+// Shared by every call in the process; each call overwrites what it reads.
+static __device__ __align__(256) double g_energy_scratch[2 * kStaticEnergyBlocks + 3];
+
+int64_t energy_static_max_leaves() { return int64_t(kStaticEnergyBlocks) * kStaticLeavesPerBlock; }
+
+cudaError_t energy_static_scratch(double** ptr) {
+  // Host code cannot use the array's name as a device address: look the
+  // address up once per device, with that device current.
+  static std::mutex mu;
+  static double* addr[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* a = nullptr;
+    e = cudaGetSymbolAddress(&a, g_energy_scratch);
+    if (e != cudaSuccess) return e;
+    addr[dev] = static_cast<double*>(a);
+  }
+  *ptr = addr[dev];
+  return cudaSuccess;
+}
+
+cudaError_t launch_energy_static(View v, const float* u, const float* p, const uint32_t* soff,
+                                 const void* samp, bool fp16, double lambda, double gamma,
+                                 double* scratch, cudaStream_t s) {
+  const int64_t want = (v.n + kStaticLeavesPerBlock - 1) / kStaticLeavesPerBlock;
+  if (want > kStaticEnergyBlocks) return cudaErrorInvalidValue;
+  const int nb = want < 1 ? 1 : int(want);
+  if (fp16)
+    k_energy<__half><<<nb, kThreads, 0, s>>>(v, u, p, soff, reinterpret_cast<const __half*>(samp),
+                                             lambda, gamma, scratch);
+  else
+    k_energy<float><<<nb, kThreads, 0, s>>>(v, u, p, soff, reinterpret_cast<const float*>(samp),
+                                            lambda, gamma, scratch);
+  count_launches(1);
+  k_energy_final<<<1, 32, 0, s>>>(scratch, nb, scratch + 2 * kStaticEnergyBlocks);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+int energy_static_result_offset() { return 2 * kStaticEnergyBlocks; }
 
 }  // namespace ofu

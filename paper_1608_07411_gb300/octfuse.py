@@ -69,6 +69,7 @@ _SIGS = {
     "ofu_export_neighbours": (_i32, [_vp, _i32, _vp, _vp, _i64, _P64]),
     "ofu_import_leaves": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp]),
     "ofu_set_state": (_i32, [_vp, _vp, _vp, _vp, _i64]),
+    "ofu_energy_static": (_i32, [_vp, _vp]),
     "ofu_kernel_launches": (_i64, []),
     "ofu_profile": (_i32, [_vp, _i32]),
     "ofu_profile_read": (_i32, [_vp, _PD, _P64, _PD]),
@@ -202,6 +203,16 @@ def ofu_import_leaves(ctx, keys, levels, n, u=None, p=None) -> None:
 
 def ofu_set_state(ctx, u, ubar, p, n) -> None:
     _check(ctx, load().ofu_set_state(ctx, _ptr(u), _ptr(ubar), _ptr(p), n))
+
+
+def ofu_energy_static(ctx, out3=None):
+    """Energy without any device allocation; `out3` (host or device, 3 float64)
+    receives primal, dual, gap.  Without `out3` a host array is returned."""
+    host = out3 is None
+    if host:
+        out3 = np.zeros(3, np.float64)
+    _check(ctx, load().ofu_energy_static(ctx, _ptr(out3)))
+    return tuple(float(x) for x in out3) if host else out3
 
 
 def ofu_kernel_launches() -> int:
