@@ -26,7 +26,7 @@ thread_local std::string g_create_error;
 // Persistent device buffers by role (content not kept across growth).
 enum Buf {
   B_SCAN, B_U0, B_PYR, B_FLAGS, B_POS, B_CNT, B_OVFC, B_CLS, B_OUTC, B_JL, B_SRC, B_LIST,
-  B_SMALL, B_PART, B_NUM
+  B_SMALL, B_PART, B_BIG, B_LONGQ, B_NUM
 };
 
 struct Bufs {
@@ -132,6 +132,7 @@ View view_of(const ofu_ctx* ctx) {
   v.nbr = L.nbr;
   v.ovf = ctx->ovf;
   v.stride = L.cap;
+  v.map = ctx->map;
   return v;
 }
 
@@ -157,15 +158,35 @@ int64_t max_leaves(const ofu_ctx* ctx) {
   return ctx->prm.max_leaves > 0 ? std::min<int64_t>(ctx->prm.max_leaves, kMaxLeaves) : kMaxLeaves;
 }
 
-// Face neighbours and step sizes of the current structure.
+// Voxel -> leaf map of the current structure.
+ofu_status rebuild_map(ofu_ctx* ctx) {
+  const int D = ctx->prm.max_depth;
+  if (!ctx->map) CU(cudaMalloc(&ctx->map, (size_t(1) << (3 * D)) * sizeof(uint32_t)));
+  uint32_t* big;
+  uint64_t* small;
+  ST(ensure(ctx, B_BIG, size_t(ctx->n), &big));
+  ST(ensure(ctx, B_SMALL, 8, &small));
+  Leaves& L = ctx->L[ctx->cur];
+  CU(launch_map(L.key, L.level, ctx->n, D, ctx->map, big,
+                reinterpret_cast<unsigned long long*>(small + 5), ctx->stream));
+  return OFU_OK;
+}
+
+// Voxel map, face neighbours and step sizes of the current structure.
 ofu_status rebuild_topology(ofu_ctx* ctx) {
   const int64_t n = ctx->n;
+  ST(rebuild_map(ctx));
   uint32_t* ovfc;
   uint32_t* tmp;
   ST(ensure(ctx, B_OVFC, size_t(6 * n + 1), &ovfc));
   ST(ensure(ctx, B_SCAN, scan_tmp_items<uint32_t>(6 * n) * 2, &tmp));
+  uint32_t* longq;
+  uint64_t* small;
+  ST(ensure(ctx, B_LONGQ, size_t(6 * n), &longq));
+  ST(ensure(ctx, B_SMALL, 8, &small));
+  unsigned long long* nlong = reinterpret_cast<unsigned long long*>(small + 8);
   View v = view_of(ctx);
-  CU(launch_nbr_count(v, ovfc, ctx->stream));
+  CU(launch_nbr_count(v, ovfc, longq, nlong, ctx->stream));
   CU(scan_exclusive<uint32_t>(ovfc, ovfc, 6 * n, tmp, ctx->stream));
   uint32_t total = 0;
   ST(read_back(ctx, ovfc + 6 * n, sizeof(uint32_t), &total));
@@ -179,9 +200,25 @@ ofu_status rebuild_topology(ofu_ctx* ctx) {
   }
   v = view_of(ctx);
   Leaves& L = ctx->L[ctx->cur];
-  CU(launch_nbr_fill(v, ovfc, L.nbr, ctx->ovf, ctx->stream));
+  CU(launch_nbr_fill(v, ovfc, L.nbr, ctx->ovf, longq, nlong, ctx->stream));
   v = view_of(ctx);
-  CU(launch_precond(v, L.tau, L.sigma, ctx->stream));
+  // heavy leaves (long face lists) for the step sizes and iteration kernels
+  if (ctx->heavy_cap < n) {
+    if (ctx->heavy) CU(cudaFree(ctx->heavy));
+    ctx->heavy = nullptr;
+    ctx->heavy_cap = 0;
+    const int64_t cap = std::max<int64_t>(n + n / 4, 1024);
+    CU(cudaMalloc(&ctx->heavy, 2 * size_t(cap) * sizeof(uint32_t)));
+    ctx->heavy_cap = cap;
+  }
+  CU(launch_heavy(v, ctx->heavy, ctx->heavy + ctx->heavy_cap,
+                  reinterpret_cast<unsigned long long*>(small + 6), ctx->stream));
+  uint64_t hc[2];
+  ST(read_back(ctx, small + 6, 2 * sizeof(uint64_t), hc));
+  ctx->n_heavy_dual = int(hc[0]);
+  ctx->n_heavy_primal = int(hc[1]);
+  CU(launch_precond(v, L.tau, L.sigma, ctx->heavy + ctx->heavy_cap, ctx->n_heavy_primal,
+                    ctx->stream));
   return OFU_OK;
 }
 
@@ -298,6 +335,8 @@ void ofu_destroy(ofu_ctx* ctx) {
   cudaFree(ctx->ovf);
   cudaFree(ctx->depth);
   cudaFree(ctx->cams);
+  cudaFree(ctx->map);
+  cudaFree(ctx->heavy);
   if (ctx->scratch) {
     Bufs& B = bufs(ctx);
     for (int b = 0; b < B_NUM; ++b) cudaFree(B.p[b]);
@@ -404,10 +443,12 @@ ofu_status ofu_iterate(ofu_ctx* ctx, int32_t n) {
       ctx->prof_used += 3;
       CU(cudaEventRecord(ev[0], ctx->stream));
     }
-    CU(launch_dual(v, L.ubar, L.p, L.sigma, float(ctx->prm.lambda), ctx->stream));
+    CU(launch_dual(v, L.ubar, L.p, L.sigma, float(ctx->prm.lambda), ctx->heavy,
+                   ctx->n_heavy_dual, ctx->stream));
     if (ctx->prof_on) CU(cudaEventRecord(ev[1], ctx->stream));
     CU(launch_primal(v, L.u, L.ubar, L.p, L.tau, L.soff, ctx->samp[ctx->cur], h16,
-                     float(ctx->prm.gamma), ctx->stream));
+                     float(ctx->prm.gamma), ctx->heavy + ctx->heavy_cap, ctx->n_heavy_primal,
+                     ctx->stream));
     if (ctx->prof_on) {
       CU(cudaEventRecord(ev[2], ctx->stream));
       ctx->prof_launches[0] += 1;
@@ -461,8 +502,10 @@ ofu_status ofu_restructure(ofu_ctx* ctx, int64_t* n_split, int64_t* n_join, int6
   ST(ensure(ctx, B_SCAN, std::max(scan_tmp_items<uint64_t>(n) * 2, scan_tmp_items<uint32_t>(n_new) * 2 / 2 + 1), &tmp64));
   tmp32 = reinterpret_cast<uint32_t*>(tmp64);
   v = view_of(ctx);
-  CU(launch_emit(v, L.u, L.p, outc, jl, n_new, N2.key, N2.level, N2.u, N2.ubar, N2.p, N2.cap, src,
-                 ctx->stream));
+  uint32_t* big;
+  ST(ensure(ctx, B_BIG, size_t(n), &big));
+  CU(launch_emit(v, L.u, L.p, outc, jl, N2.key, N2.level, N2.u, N2.ubar, N2.p, N2.cap, src, big,
+                 reinterpret_cast<unsigned long long*>(small + 4), ctx->stream));
   CU(cudaMemsetAsync(small + 3, 0, sizeof(uint64_t), ctx->stream));
   CU(launch_new_list(src, n_new, list, reinterpret_cast<unsigned long long*>(small + 3), ctx->stream));
   CU(launch_kept_counts(src, L.soff, n_new, N2.soff, ctx->stream));

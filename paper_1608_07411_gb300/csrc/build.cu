@@ -388,82 +388,53 @@ __global__ void __launch_bounds__(256) k_leaf_fill(
 }
 
 // ---------------------------------------------------------------------------
-// Search in the sorted key array: largest i with key[i] <= q, galloping from
-// `hint` (neighbours are usually close in Morton order).  key[0] == 0 <= q.
+// Voxel map: for every finest voxel (Morton order) the index of the leaf that
+// contains it.  Leaves cover contiguous key ranges [key, key + h^3), so the
+// map turns "which leaf holds this point" into one load.  Small leaves are
+// written by one thread each, larger ones by a block each.
 
-__device__ __forceinline__ int64_t locate(const uint64_t* __restrict__ key, int64_t n, uint64_t q,
-                                          int64_t hint) {
-  int64_t lo, hi;
-  if (key[hint] <= q) {
-    lo = hint;
-    int64_t step = 1;
-    for (;;) {
-      const int64_t t = lo + step;
-      if (t >= n) { hi = n; break; }
-      if (key[t] <= q) { lo = t; step <<= 1; } else { hi = t; break; }
+constexpr uint32_t kSmallFill = 64;
+
+__global__ void k_map_small(const uint64_t* __restrict__ key, const uint8_t* __restrict__ level,
+                            int64_t n, int D, uint32_t* __restrict__ map, uint32_t* __restrict__ big,
+                            unsigned long long* __restrict__ nbig) {
+  const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (l >= n) return;
+  const uint64_t k = key[l];
+  const uint64_t h3 = uint64_t(1) << (3 * (D - level[l]));
+  if (h3 <= kSmallFill) {
+    if (h3 >= 4) {
+      const uint4 w = make_uint4(uint32_t(l), uint32_t(l), uint32_t(l), uint32_t(l));
+      uint4* m4 = reinterpret_cast<uint4*>(map + k);
+      for (uint64_t j = 0; j < h3 / 4; ++j) m4[j] = w;
+    } else {
+      map[k] = uint32_t(l);
     }
   } else {
-    hi = hint;
-    int64_t step = 1;
-    for (;;) {
-      int64_t t = hi - step;
-      if (t <= 0) { lo = 0; break; }
-      if (key[t] <= q) { lo = t; break; }
-      hi = t;
-      step <<= 1;
-    }
+    big[atomicAdd(nbig, 1ull)] = uint32_t(l);
   }
-  while (hi - lo > 1) {
-    const int64_t mid = lo + ((hi - lo) >> 1);
-    if (key[mid] <= q) lo = mid; else hi = mid;
-  }
-  return lo;
 }
 
-// Finer neighbours across a face, in ascending key order: depth-first walk of
-// the same-size neighbour cube restricted to the octants on the face.
-// `side` is the bit the face octants have on `axis` (0: the cube's low side).
-template <bool WRITE>
-__device__ uint32_t finer_face_list(const View& v, uint64_t cube_key, int cube_level, int axis,
-                                    int side, int64_t hint, int32_t* out) {
-  uint64_t sk[64];
-  int8_t sl[64];
-  int sp = 0;
-  auto push_children = [&](uint64_t k, int L) {
-    const uint64_t csz = uint64_t(1) << (3 * (v.D - L - 1));
-    for (int c = 7; c >= 0; --c) {
-      if (((c >> axis) & 1) != side) continue;
-      if (sp < 64) {
-        sk[sp] = k + uint64_t(c) * csz;
-        sl[sp] = int8_t(L + 1);
-        ++sp;
-      }
-    }
-  };
-  push_children(cube_key, cube_level);
-  uint32_t cnt = 0;
-  while (sp > 0) {
-    --sp;
-    const uint64_t k = sk[sp];
-    const int L = sl[sp];
-    const int64_t i = locate(v.key, v.n, k, hint);
-    hint = i;
-    const int li = v.level[i];
-    if (li <= L || L >= v.D || sp > 60) {
-      if (WRITE) out[cnt] = make_single(uint32_t(i), li);
-      ++cnt;
-    } else {
-      push_children(k, L);
-    }
+__global__ void k_map_big(const uint64_t* __restrict__ key, const uint8_t* __restrict__ level,
+                          const uint32_t* __restrict__ big, const unsigned long long* __restrict__ nbig,
+                          int D, uint32_t* __restrict__ map) {
+  // blockIdx.y walks the queued leaves, blockIdx.x the 4096-voxel chunks of one
+  const unsigned long long nb = *nbig;
+  for (unsigned long long b = blockIdx.y; b < nb; b += gridDim.y) {
+    const uint32_t l = big[b];
+    const uint64_t k = key[l];
+    const uint64_t h34 = (uint64_t(1) << (3 * (D - level[l]))) / 4;
+    const uint4 w = make_uint4(l, l, l, l);
+    uint4* m4 = reinterpret_cast<uint4*>(map + k);
+    for (uint64_t c = uint64_t(blockIdx.x) * 1024; c < h34; c += uint64_t(gridDim.x) * 1024)
+      for (uint64_t j = c + threadIdx.x; j < c + 1024 && j < h34; j += blockDim.x) m4[j] = w;
   }
-  return cnt;
 }
 
 struct FaceHit {
   int kind;  // 0 empty, 1 single, 2 finer list
-  int64_t m;
+  uint32_t m;
   int mlev;
-  uint64_t cube;
 };
 
 __device__ __forceinline__ FaceHit face_query(const View& v, int64_t l, int face) {
@@ -477,24 +448,83 @@ __device__ __forceinline__ FaceHit face_query(const View& v, int64_t l, int face
   const int axis = face % 3;
   c[axis] += face < 3 ? h : -h;
   if (c[axis] < 0 || c[axis] >= n1) return r;
-  const uint64_t q = morton(uint32_t(c[0]), uint32_t(c[1]), uint32_t(c[2]));
-  const int64_t m = locate(v.key, v.n, q, l);
-  r.m = m;
-  r.mlev = v.level[m];
-  r.cube = q;
+  r.m = v.map[morton(uint32_t(c[0]), uint32_t(c[1]), uint32_t(c[2]))];
+  r.mlev = v.level[r.m];
   r.kind = r.mlev <= lev ? 1 : 2;
   return r;
 }
 
-__global__ void k_nbr_count(View v, uint32_t* __restrict__ ovf_count) {
+// Finer neighbours across a face.  The finest voxels just outside the face
+// form an h x h square; leaf m touching the face is listed once, at the face
+// voxel matching m's corner in the two tangential axes.  Enumerating the
+// square in 2-D Morton order of the tangential coordinates (lower axis index
+// = lower bit) yields the leaves in ascending key order: along the path to
+// every such leaf the bit of the face axis is the same at each level (all on
+// one side of the neighbour cube), so keys compare by the tangential bits.
+struct FaceSquare {
+  int t1, t2;          // tangential axes, t1 < t2
+  uint32_t c1, c2;     // corner of the square on t1, t2
+  uint32_t cax;        // the face voxels' coordinate on the face axis
+  int axis;
+  uint32_t h;          // square edge
+};
+
+__device__ __forceinline__ FaceSquare face_square(const View& v, int64_t l, int face) {
+  FaceSquare q;
+  const uint64_t k = v.key[l];
+  const uint32_t c[3] = {compact3(k), compact3(k >> 1), compact3(k >> 2)};
+  q.h = 1u << (v.D - v.level[l]);
+  q.axis = face % 3;
+  q.t1 = q.axis == 0 ? 1 : 0;
+  q.t2 = q.axis == 2 ? 1 : 2;
+  q.c1 = c[q.t1];
+  q.c2 = c[q.t2];
+  q.cax = face < 3 ? c[q.axis] + q.h : c[q.axis] - 1;
+  return q;
+}
+
+__device__ __forceinline__ uint32_t even_bits(uint32_t x) {
+  x &= 0x55555555u;
+  x = (x | (x >> 1)) & 0x33333333u;
+  x = (x | (x >> 2)) & 0x0f0f0f0fu;
+  x = (x | (x >> 4)) & 0x00ff00ffu;
+  x = (x | (x >> 8)) & 0x0000ffffu;
+  return x;
+}
+
+// Leaf listed at face voxel i (2-D Morton index), or -1.
+__device__ __forceinline__ int64_t face_rep(const View& v, const FaceSquare& q, uint32_t i) {
+  const uint32_t a = q.c1 + even_bits(i), b = q.c2 + even_bits(i >> 1);
+  uint32_t c[3];
+  c[q.axis] = q.cax;
+  c[q.t1] = a;
+  c[q.t2] = b;
+  const uint32_t m = v.map[morton(c[0], c[1], c[2])];
+  const uint64_t km = v.key[m];
+  return (compact3(km >> q.t1) == a && compact3(km >> q.t2) == b) ? int64_t(m) : -1;
+}
+
+// Lists of squares up to kThreadSquare voxels are walked by one thread;
+// larger ones by a block (k_nbr_long_*).
+constexpr uint32_t kThreadSquare = 16;
+
+__global__ void k_nbr_count(View v, uint32_t* __restrict__ ovf_count, uint32_t* __restrict__ longq,
+                            unsigned long long* __restrict__ nlong) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= 6 * v.n) return;
   const int face = int(t / v.n);
   const int64_t l = t - int64_t(face) * v.n;
   const FaceHit f = face_query(v, l, face);
   uint32_t c = 0;
-  if (f.kind == 2)
-    c = 1 + finer_face_list<false>(v, f.cube, v.level[l], face % 3, face < 3 ? 0 : 1, f.m, nullptr);
+  if (f.kind == 2) {
+    const FaceSquare q = face_square(v, l, face);
+    if (q.h * q.h > kThreadSquare) {
+      longq[atomicAdd(nlong, 1ull)] = uint32_t(t);   // counted by k_nbr_long_count
+    } else {
+      c = 1;
+      for (uint32_t i = 0; i < q.h * q.h; ++i) c += face_rep(v, q, i) >= 0;
+    }
+  }
   ovf_count[t] = c;
 }
 
@@ -507,62 +537,208 @@ __global__ void k_nbr_fill(View v, const uint32_t* __restrict__ ovf_off, int32_t
   const FaceHit f = face_query(v, l, face);
   int32_t e = kEmpty;
   if (f.kind == 1) {
-    e = make_single(uint32_t(f.m), f.mlev);
+    e = make_single(f.m, f.mlev);
   } else if (f.kind == 2) {
     const uint32_t st = ovf_off[t];
-    const uint32_t cnt = finer_face_list<true>(v, f.cube, v.level[l], face % 3, face < 3 ? 0 : 1,
-                                               f.m, ovf + st + 1);
-    ovf[st] = int32_t(cnt);
     e = make_list(st);
+    const FaceSquare q = face_square(v, l, face);
+    if (q.h * q.h <= kThreadSquare) {
+      uint32_t c = 0;
+      for (uint32_t i = 0; i < q.h * q.h; ++i) {
+        const int64_t m = face_rep(v, q, i);
+        if (m >= 0) ovf[st + 1 + c++] = make_single(uint32_t(m), v.level[m]);
+      }
+      ovf[st] = int32_t(c);
+    }
   }
   nbr[int64_t(face) * v.stride + l] = e;
 }
 
-// sqrt(2^(3k)) for integer k, exact up to the rounding of sqrt(2).
-__device__ __forceinline__ double sqrt_pow8(int k) {
+// Block-wide ordered walk of a face square: calls emit(position, leaf) for
+// each listed leaf in ascending order; returns the count in every thread.
+template <typename Emit>
+__device__ uint32_t block_face_walk(const View& v, const FaceSquare& q, Emit emit) {
+  __shared__ uint32_t wsum[8];
+  uint32_t base = 0;
+  const int lane = lane_id(), wid = threadIdx.x >> 5;
+  const uint32_t n = q.h * q.h;
+  for (uint32_t i0 = 0; i0 < n; i0 += blockDim.x) {
+    const uint32_t i = i0 + threadIdx.x;
+    const int64_t m = i < n ? face_rep(v, q, i) : -1;
+    const unsigned bal = __ballot_sync(kFull, m >= 0);
+    if (lane == 0) wsum[wid] = __popc(bal);
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+      before += w < wid ? wsum[w] : 0;
+      total += wsum[w];
+    }
+    if (m >= 0) emit(base + before + __popc(bal & ((1u << lane) - 1)), m);
+    base += total;
+    __syncthreads();
+  }
+  return base;
+}
+
+__global__ void k_nbr_long_count(View v, const uint32_t* __restrict__ longq,
+                                 const unsigned long long* __restrict__ nlong,
+                                 uint32_t* __restrict__ ovf_count) {
+  const unsigned long long nq = *nlong;
+  for (unsigned long long j = blockIdx.x; j < nq; j += gridDim.x) {
+    const uint32_t t = longq[j];
+    const int face = int(int64_t(t) / v.n);
+    const int64_t l = int64_t(t) - int64_t(face) * v.n;
+    const FaceSquare q = face_square(v, l, face);
+    const uint32_t cnt = block_face_walk(v, q, [](uint32_t, int64_t) {});
+    if (threadIdx.x == 0) ovf_count[t] = 1 + cnt;
+  }
+}
+
+__global__ void k_nbr_long_fill(View v, const uint32_t* __restrict__ longq,
+                                const unsigned long long* __restrict__ nlong,
+                                const uint32_t* __restrict__ ovf_off, int32_t* __restrict__ ovf) {
+  const unsigned long long nq = *nlong;
+  for (unsigned long long j = blockIdx.x; j < nq; j += gridDim.x) {
+    const uint32_t t = longq[j];
+    const int face = int(int64_t(t) / v.n);
+    const int64_t l = int64_t(t) - int64_t(face) * v.n;
+    const FaceSquare q = face_square(v, l, face);
+    const uint32_t st = ovf_off[t];
+    int32_t* out = ovf + st + 1;
+    const uint32_t cnt = block_face_walk(v, q, [&](uint32_t pos, int64_t m) {
+      out[pos] = make_single(uint32_t(m), v.level[m]);
+    });
+    if (threadIdx.x == 0) ovf[st] = int32_t(cnt);
+  }
+}
+
+// 2^e as float for -126 <= e <= 127 (exact).
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+// sqrt(8^k) = 2^(3k/2): exact for even k, otherwise the float sqrt(2) scaled.
+__device__ __forceinline__ float sqrt_pow8f(int k) {
   const int e = 3 * k;
-  const double base = ldexp(1.0, e >> 1);  // floor(e / 2) also for negative e
-  return (e & 1) ? base * 1.4142135623730951 : base;
+  const float b = pow2f(e >> 1);
+  return (e & 1) ? b * 1.41421356237309505f : b;
 }
 
 // Diagonal preconditioning (Pock & Chambolle 2011, alpha = 1) of the
 // volume-weighted operator: sigma_l = 1 / max over non-empty rows d of
-// sum_j |K~_(l,d),j|, tau_l = 1 / sum over rows of |K~_row,l|.
-__global__ void k_precond(View v, float* __restrict__ tau, float* __restrict__ sigma) {
-  const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+// sum_j |K~_(l,d),j|, tau_l = 1 / sum over rows of |K~_row,l|, where
+// K~ = W_p^1/2 K W_u^-1/2.  Entries of K: alpha / Delta with face share
+// alpha = min(1, (h_m / h_l)^2) and centre distance Delta = (h_l + h_m) / 2.
+// Per-face contribution of one list entry (neighbour level ml) of leaf
+// level lev: for +faces the row and diagonal terms, for -faces the column term.
+__device__ __forceinline__ void precond_terms(int face, int lev, int ml, float hl, int D,
+                                              float* row, float* diag, float* col) {
+  const float hm = pow2f(D - ml);
+  const float inv_d = 2.0f / (hl + hm);
+  if (face < 3) {
+    // alpha_lm = min(1, (h_m/h_l)^2); scale sqrt(h_l^3 / h_m^3)
+    const float w = (ml > lev ? pow2f(2 * (lev - ml)) : 1.0f) * inv_d;
+    *row += w * sqrt_pow8f(ml - lev);
+    *diag += w;
+  } else {
+    // alpha_nl = min(1, (h_l/h_n)^2); scale sqrt(h_n^3 / h_l^3)
+    const float w = (ml < lev ? pow2f(2 * (ml - lev)) : 1.0f) * inv_d;
+    *col += w * sqrt_pow8f(lev - ml);
+  }
+}
+
+__device__ __forceinline__ float block_sum_f(float x, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  __syncthreads();
+  if (lane_id() == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  float t = 0.0f;
+  for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[w];
+  return t;
+}
+
+// Diagonal preconditioning (Pock & Chambolle 2011, alpha = 1) of the
+// volume-weighted operator: sigma_l = 1 / max over non-empty rows d of
+// sum_j |K~_(l,d),j|, tau_l = 1 / sum over rows of |K~_row,l|, where
+// K~ = W_p^1/2 K W_u^-1/2.  Entries of K: alpha / Delta with face share
+// alpha = min(1, (h_m / h_l)^2) and centre distance Delta = (h_l + h_m) / 2.
+// Leaves with a list longer than kHeavy get a block each (the first
+// n_heavy blocks); the others a thread.
+__global__ void k_precond(View v, float* __restrict__ tau, float* __restrict__ sigma,
+                          const uint32_t* __restrict__ heavy, int n_heavy) {
+  if (int(blockIdx.x) < n_heavy) {
+    __shared__ float red[8];
+    const int64_t l = heavy[blockIdx.x];
+    const int lev = v.level[l];
+    const float hl = pow2f(v.D - lev);
+    float rowmax = 0.0f, col = 0.0f;
+    for (int face = 0; face < 6; ++face) {
+      const int32_t e = v.nbr[int64_t(face) * v.stride + l];
+      if (e == kEmpty) continue;
+      float row = 0.0f, diag = 0.0f, cl = 0.0f;
+      if (is_list(e)) {
+        const uint32_t st = list_start(e);
+        const int cnt = v.ovf[st];
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x)
+          precond_terms(face, lev, entry_level(v.ovf[st + 1 + k]), hl, v.D, &row, &diag, &cl);
+      } else if (threadIdx.x == 0) {
+        precond_terms(face, lev, entry_level(e), hl, v.D, &row, &diag, &cl);
+      }
+      if (face < 3) {
+        const float r = block_sum_f(row, red);
+        const float dg = block_sum_f(diag, red);
+        rowmax = fmaxf(rowmax, r + dg);
+        col += dg;
+      } else {
+        col += block_sum_f(cl, red);
+      }
+    }
+    if (threadIdx.x == 0) {
+      sigma[l] = rowmax > 0.0f ? 1.0f / rowmax : 0.0f;
+      tau[l] = col > 0.0f ? 1.0f / col : 1.0f;
+    }
+    return;
+  }
+  const int64_t l = int64_t(blockIdx.x - n_heavy) * blockDim.x + threadIdx.x;
   if (l >= v.n) return;
   const int lev = v.level[l];
-  const double hl = double(int64_t(1) << (v.D - lev));
-  double rowmax = 0.0, col = 0.0;
+  const float hl = pow2f(v.D - lev);
+  float rowmax = 0.0f, col = 0.0f;
   for (int face = 0; face < 6; ++face) {
     const int32_t e = v.nbr[int64_t(face) * v.stride + l];
     if (e == kEmpty) continue;
-    uint32_t cnt = 1;
-    const int32_t* lst = &e;
+    float row = 0.0f, diag = 0.0f;
     if (is_list(e)) {
-      cnt = uint32_t(v.ovf[list_start(e)]);
-      lst = v.ovf + list_start(e) + 1;
-    }
-    double row = 0.0, diag = 0.0;
-    for (uint32_t k = 0; k < cnt; ++k) {
-      const int ml = entry_level(lst[k]);
-      const double hm = double(int64_t(1) << (v.D - ml));
-      const double w = face < 3 ? fmin(1.0, (hm / hl) * (hm / hl)) / ((hl + hm) * 0.5)
-                                : fmin(1.0, (hl / hm) * (hl / hm)) / ((hl + hm) * 0.5);
-      if (face < 3) {
-        row += w * sqrt_pow8(ml - lev);   // sqrt(h_l^3 / h_m^3)
-        diag += w;
-      } else {
-        col += w * sqrt_pow8(lev - ml);   // sqrt(h_n^3 / h_l^3)
-      }
+      const uint32_t st = list_start(e);
+      const int cnt = v.ovf[st];
+      if (cnt > kHeavy) return;   // a heavy block computes this leaf
+      for (int k = 0; k < cnt; ++k)
+        precond_terms(face, lev, entry_level(v.ovf[st + 1 + k]), hl, v.D, &row, &diag, &col);
+    } else {
+      precond_terms(face, lev, entry_level(e), hl, v.D, &row, &diag, &col);
     }
     if (face < 3) {
-      rowmax = fmax(rowmax, row + diag);
+      rowmax = fmaxf(rowmax, row + diag);
       col += diag;
     }
   }
-  sigma[l] = rowmax > 0.0 ? float(1.0 / rowmax) : 0.0f;
-  tau[l] = col > 0.0 ? float(1.0 / col) : 1.0f;
+  sigma[l] = rowmax > 0.0f ? 1.0f / rowmax : 0.0f;
+  tau[l] = col > 0.0f ? 1.0f / col : 1.0f;
+}
+
+__global__ void k_heavy(View v, uint32_t* __restrict__ hd, uint32_t* __restrict__ hp,
+                        unsigned long long* __restrict__ counts) {
+  const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (l >= v.n) return;
+  bool dual = false, primal = false;
+  for (int face = 0; face < 6; ++face) {
+    const int32_t e = v.nbr[int64_t(face) * v.stride + l];
+    if (is_list(e) && v.ovf[list_start(e)] > kHeavy) {
+      primal = true;
+      if (face < 3) dual = true;
+    }
+  }
+  if (dual) hd[atomicAdd(&counts[0], 1ull)] = uint32_t(l);
+  if (primal) hp[atomicAdd(&counts[1], 1ull)] = uint32_t(l);
 }
 
 __global__ void k_check_tiling(const uint64_t* __restrict__ key, const uint8_t* __restrict__ level,
@@ -591,6 +767,11 @@ __global__ void k_classify(const float* __restrict__ u, int64_t n, double tau_j,
   cls[l] = (x > tau_j ? (uint64_t(1) << 32) : 0) | (x < -tau_j ? 1u : 0u);
 }
 
+// Marks: a leaf joins into the coarsest ancestor whose leaves all carry its
+// class (checked finest-first: once an ancestor fails, every coarser one
+// fails too), else splits to the finest level when |u| < tau_s, else stays.
+// out_count is the number of new leaves it emits (join: 1 for the group's
+// first leaf, 0 for the others).
 __global__ void k_mark(View v, const float* __restrict__ u, const uint64_t* __restrict__ cscan,
                        double tau_s, double tau_j, uint64_t* __restrict__ out_count,
                        int8_t* __restrict__ join_level, unsigned long long* __restrict__ counters) {
@@ -602,12 +783,11 @@ __global__ void k_mark(View v, const float* __restrict__ u, const uint64_t* __re
   int jl = -1;
   int64_t jlo = 0;
   if (cls != 0) {
-    // finest ancestor first; a node that fails makes every coarser one fail
     for (int L = lev - 1; L >= 0; --L) {
       const uint64_t sz = uint64_t(1) << (3 * (v.D - L));
       const uint64_t a = v.key[l] & ~(sz - 1);
-      const int64_t lo = locate(v.key, v.n, a, l);
-      const int64_t hi = locate(v.key, v.n, a + sz - 1, l) + 1;
+      const int64_t lo = v.map[a];
+      const int64_t hi = int64_t(v.map[a + sz - 1]) + 1;
       const uint64_t d = cscan[hi] - cscan[lo];
       const uint64_t want = uint64_t(hi - lo);
       const bool ok = cls > 0 ? (d >> 32) == want : (d & 0xffffffffull) == want;
@@ -630,55 +810,144 @@ __global__ void k_mark(View v, const float* __restrict__ u, const uint64_t* __re
   join_level[l] = int8_t(jl);
 }
 
-// One thread per new leaf: find its source leaf in the exclusive scan of the
-// output counts (the last leaf whose offset is <= j).
+constexpr uint64_t kSmallEmit = 64;
+
+// One thread per old leaf writes the new leaves it produces at its offset:
+// kept leaves copy themselves, small splits write their finest children
+// (inheriting u and p), small joins write the volume-weighted means.  Splits
+// or joins of more than kSmallEmit leaves are queued for k_emit_big.
 __global__ void k_emit(View v, const float* __restrict__ u, const float* __restrict__ p,
                        const uint64_t* __restrict__ off, const int8_t* __restrict__ join_level,
-                       int64_t n_new, uint64_t* __restrict__ nkey, uint8_t* __restrict__ nlevel,
+                       uint64_t* __restrict__ nkey, uint8_t* __restrict__ nlevel,
                        float* __restrict__ nu, float* __restrict__ nubar, float* __restrict__ np_,
-                       int64_t nstride, int32_t* __restrict__ src) {
-  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (j >= n_new) return;
-  int64_t lo = 0, hi = v.n;  // off[lo] <= j < off[hi]
-  while (hi - lo > 1) {
-    const int64_t mid = lo + ((hi - lo) >> 1);
-    if (off[mid] <= uint64_t(j)) lo = mid; else hi = mid;
-  }
-  const int64_t i = lo;
+                       int64_t nstride, int32_t* __restrict__ src, uint32_t* __restrict__ big,
+                       unsigned long long* __restrict__ nbig) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= v.n) return;
+  const uint64_t o = off[i];
+  const uint64_t oc = off[i + 1] - o;
+  if (oc == 0) return;
   const int jl = join_level[i];
-  const int lev = v.level[i];
+  const float ui = u[i];
+  const float p0 = p[i], p1 = p[v.stride + i], p2 = p[2 * v.stride + i];
   if (jl >= 0) {
     const uint64_t sz = uint64_t(1) << (3 * (v.D - jl));
     const uint64_t a = v.key[i] & ~(sz - 1);
-    const int64_t e = locate(v.key, v.n, a + sz - 1, i) + 1;
-    double su = 0.0, sp[3] = {0.0, 0.0, 0.0}, sw = 0.0;
+    const int64_t e = int64_t(v.map[a + sz - 1]) + 1;
+    if (uint64_t(e - i) > kSmallEmit) {
+      big[atomicAdd(nbig, 1ull)] = uint32_t(i);
+      return;
+    }
+    double su = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0, sw = 0.0;
     for (int64_t k = i; k < e; ++k) {
       const double w = double(uint64_t(1) << (3 * (v.D - v.level[k])));
       su += w * double(u[k]);
-      for (int d = 0; d < 3; ++d) sp[d] += w * double(p[int64_t(d) * v.stride + k]);
+      s0 += w * double(p[k]);
+      s1 += w * double(p[v.stride + k]);
+      s2 += w * double(p[2 * v.stride + k]);
       sw += w;
     }
-    nkey[j] = a;
-    nlevel[j] = uint8_t(jl);
-    nu[j] = float(su / sw);
-    nubar[j] = float(su / sw);
-    for (int d = 0; d < 3; ++d) np_[int64_t(d) * nstride + j] = float(sp[d] / sw);
-    src[j] = -1;
-  } else {
-    // a split leaf emits 8^(D - level) > 1 children; a kept one emits 1
-    const uint64_t cnt = off[i + 1] - off[i];
-    if (cnt > 1) {
-      nkey[j] = v.key[i] + (uint64_t(j) - off[i]);
-      nlevel[j] = uint8_t(v.D);
-      src[j] = -1;
+    nkey[o] = a;
+    nlevel[o] = uint8_t(jl);
+    nu[o] = float(su / sw);
+    nubar[o] = float(su / sw);
+    np_[o] = float(s0 / sw);
+    np_[nstride + o] = float(s1 / sw);
+    np_[2 * nstride + o] = float(s2 / sw);
+    src[o] = -1;
+    return;
+  }
+  if (oc == 1) {
+    nkey[o] = v.key[i];
+    nlevel[o] = v.level[i];
+    nu[o] = ui;
+    nubar[o] = ui;
+    np_[o] = p0;
+    np_[nstride + o] = p1;
+    np_[2 * nstride + o] = p2;
+    src[o] = int32_t(i);
+    return;
+  }
+  if (oc > kSmallEmit) {
+    big[atomicAdd(nbig, 1ull)] = uint32_t(i);
+    return;
+  }
+  const uint64_t k0 = v.key[i];
+  for (uint64_t c = 0; c < oc; ++c) {
+    nkey[o + c] = k0 + c;
+    nlevel[o + c] = uint8_t(v.D);
+    nu[o + c] = ui;
+    nubar[o + c] = ui;
+    np_[o + c] = p0;
+    np_[nstride + o + c] = p1;
+    np_[2 * nstride + o + c] = p2;
+    src[o + c] = -1;
+  }
+}
+
+// Block per queued large split or join.
+__global__ void k_emit_big(View v, const float* __restrict__ u, const float* __restrict__ p,
+                           const uint64_t* __restrict__ off, const int8_t* __restrict__ join_level,
+                           uint64_t* __restrict__ nkey, uint8_t* __restrict__ nlevel,
+                           float* __restrict__ nu, float* __restrict__ nubar,
+                           float* __restrict__ np_, int64_t nstride, int32_t* __restrict__ src,
+                           const uint32_t* __restrict__ big,
+                           const unsigned long long* __restrict__ nbig) {
+  __shared__ double red[5][32];
+  const unsigned long long nb = *nbig;
+  for (unsigned long long b = blockIdx.x; b < nb; b += gridDim.x) {
+    const int64_t i = big[b];
+    const uint64_t o = off[i];
+    const int jl = join_level[i];
+    if (jl >= 0) {
+      const uint64_t sz = uint64_t(1) << (3 * (v.D - jl));
+      const uint64_t a = v.key[i] & ~(sz - 1);
+      const int64_t e = int64_t(v.map[a + sz - 1]) + 1;
+      double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int64_t k = i + threadIdx.x; k < e; k += blockDim.x) {
+        const double w = double(uint64_t(1) << (3 * (v.D - v.level[k])));
+        acc[0] += w * double(u[k]);
+        acc[1] += w * double(p[k]);
+        acc[2] += w * double(p[v.stride + k]);
+        acc[3] += w * double(p[2 * v.stride + k]);
+        acc[4] += w;
+      }
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        for (int s = 16; s > 0; s >>= 1) acc[q] += __shfl_xor_sync(kFull, acc[q], s);
+        if (lane_id() == 0) red[q][threadIdx.x >> 5] = acc[q];
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < int(blockDim.x >> 5); ++w)
+          for (int q = 0; q < 5; ++q) t[q] += red[q][w];
+        nkey[o] = a;
+        nlevel[o] = uint8_t(jl);
+        nu[o] = float(t[0] / t[4]);
+        nubar[o] = float(t[0] / t[4]);
+        np_[o] = float(t[1] / t[4]);
+        np_[nstride + o] = float(t[2] / t[4]);
+        np_[2 * nstride + o] = float(t[3] / t[4]);
+        src[o] = -1;
+      }
+      __syncthreads();
     } else {
-      nkey[j] = v.key[i];
-      nlevel[j] = uint8_t(lev);
-      src[j] = int32_t(i);
+      const uint64_t oc = off[i + 1] - o;
+      const uint64_t k0 = v.key[i];
+      const float ui = u[i];
+      const float p0 = p[i], p1 = p[v.stride + i], p2 = p[2 * v.stride + i];
+      for (uint64_t c = threadIdx.x; c < oc; c += blockDim.x) {
+        nkey[o + c] = k0 + c;
+        nlevel[o + c] = uint8_t(v.D);
+        nu[o + c] = ui;
+        nubar[o + c] = ui;
+        np_[o + c] = p0;
+        np_[nstride + o + c] = p1;
+        np_[2 * nstride + o + c] = p2;
+        src[o + c] = -1;
+      }
     }
-    nu[j] = u[i];
-    nubar[j] = u[i];
-    for (int d = 0; d < 3; ++d) np_[int64_t(d) * nstride + j] = p[int64_t(d) * v.stride + i];
   }
 }
 
@@ -698,17 +967,28 @@ __global__ void k_kept_counts(const int32_t* __restrict__ src, const uint32_t* _
   if (s >= 0) count[j] = old_soff[s + 1] - old_soff[s];
 }
 
+// Samples of kept leaves into the new CSR.  A warp takes 32 consecutive new
+// leaves; when they are 32 kept leaves with consecutive sources (the common
+// case) their samples are one contiguous run in both arrays and are copied
+// coalesced, otherwise each lane copies its own leaf's samples.
 template <typename T>
 __global__ void k_copy_kept(const int32_t* __restrict__ src, int64_t n,
                             const uint32_t* __restrict__ old_soff, const T* __restrict__ old_samp,
                             const uint32_t* __restrict__ new_soff, T* __restrict__ new_samp) {
   const int warp = threadIdx.x >> 5, lane = lane_id();
-  for (int64_t j = int64_t(blockIdx.x) * kWarpsPerBlock + warp; j < n;
-       j += int64_t(gridDim.x) * kWarpsPerBlock) {
-    const int32_t s = src[j];
-    if (s < 0) continue;
-    const uint32_t a = old_soff[s], c = old_soff[s + 1] - a, b = new_soff[j];
-    for (uint32_t k = lane; k < c; k += 32) new_samp[b + k] = old_samp[a + k];
+  for (int64_t j0 = (int64_t(blockIdx.x) * kWarpsPerBlock + warp) * 32; j0 < n;
+       j0 += int64_t(gridDim.x) * kWarpsPerBlock * 32) {
+    const int64_t j = j0 + lane;
+    const int32_t sj = j < n ? src[j] : -1;
+    const int32_t s0 = __shfl_sync(kFull, sj, 0);
+    const bool run = __all_sync(kFull, j < n && s0 >= 0 && sj == s0 + lane);
+    if (run) {
+      const uint32_t a = old_soff[s0], c = old_soff[s0 + 32] - a, b = new_soff[j0];
+      for (uint32_t k = lane; k < c; k += 32) new_samp[b + k] = old_samp[a + k];
+    } else if (sj >= 0) {
+      const uint32_t a = old_soff[sj], c = old_soff[sj + 1] - a, b = new_soff[j];
+      for (uint32_t k = 0; k < c; ++k) new_samp[b + k] = old_samp[a + k];
+    }
   }
 }
 
@@ -892,24 +1172,42 @@ cudaError_t launch_leaf_fill(const uint64_t* key, const uint8_t* level, const ui
               : leaf_fill_t<float>(key, level, list, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
 }
 
-cudaError_t launch_nbr_count(View v, uint32_t* ovf_count, cudaStream_t s) {
+cudaError_t launch_nbr_count(View v, uint32_t* ovf_count, uint32_t* longq,
+                             unsigned long long* nlong, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
-  k_nbr_count<<<blocks_for(6 * v.n, 256), 256, 0, s>>>(v, ovf_count);
+  cudaError_t e = cudaMemsetAsync(nlong, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_nbr_count<<<blocks_for(6 * v.n, 256), 256, 0, s>>>(v, ovf_count, longq, nlong);
+  count_launches(1);
+  k_nbr_long_count<<<unsigned(sm_count() * 8), 256, 0, s>>>(v, longq, nlong, ovf_count);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_nbr_fill(View v, const uint32_t* ovf_off, int32_t* nbr, int32_t* ovf,
+                            const uint32_t* longq, const unsigned long long* nlong,
                             cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
   k_nbr_fill<<<blocks_for(6 * v.n, 256), 256, 0, s>>>(v, ovf_off, nbr, ovf);
   count_launches(1);
+  k_nbr_long_fill<<<unsigned(sm_count() * 8), 256, 0, s>>>(v, longq, nlong, ovf_off, ovf);
+  count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_precond(View v, float* tau, float* sigma, cudaStream_t s) {
+cudaError_t launch_precond(View v, float* tau, float* sigma, const uint32_t* heavy, int n_heavy,
+                           cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
-  k_precond<<<blocks_for(v.n, 256), 256, 0, s>>>(v, tau, sigma);
+  k_precond<<<blocks_for(v.n, 256) + n_heavy, 256, 0, s>>>(v, tau, sigma, heavy, n_heavy);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_heavy(View v, uint32_t* heavy_dual, uint32_t* heavy_primal,
+                         unsigned long long* counts, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess || v.n <= 0) return e;
+  k_heavy<<<blocks_for(v.n, 256), 256, 0, s>>>(v, heavy_dual, heavy_primal, counts);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -941,12 +1239,29 @@ cudaError_t launch_mark(View v, const float* u, const uint64_t* cls_scan, double
 }
 
 cudaError_t launch_emit(View v, const float* u, const float* p, const uint64_t* out_off,
-                        const int8_t* join_level, int64_t n_new, uint64_t* nkey, uint8_t* nlevel,
-                        float* nu, float* nubar, float* np_, int64_t nstride, int32_t* src,
-                        cudaStream_t s) {
-  if (n_new <= 0) return cudaSuccess;
-  k_emit<<<blocks_for(n_new, 256), 256, 0, s>>>(v, u, p, out_off, join_level, n_new, nkey, nlevel,
-                                                 nu, nubar, np_, nstride, src);
+                        const int8_t* join_level, uint64_t* nkey, uint8_t* nlevel, float* nu,
+                        float* nubar, float* np_, int64_t nstride, int32_t* src, uint32_t* big,
+                        unsigned long long* nbig, cudaStream_t s) {
+  if (v.n <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(nbig, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_emit<<<blocks_for(v.n, 256), 256, 0, s>>>(v, u, p, out_off, join_level, nkey, nlevel, nu, nubar,
+                                              np_, nstride, src, big, nbig);
+  count_launches(1);
+  k_emit_big<<<unsigned(sm_count() * 2), 256, 0, s>>>(v, u, p, out_off, join_level, nkey, nlevel,
+                                                      nu, nubar, np_, nstride, src, big, nbig);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_map(const uint64_t* key, const uint8_t* level, int64_t n, int D, uint32_t* map,
+                       uint32_t* big, unsigned long long* nbig, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(nbig, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_map_small<<<blocks_for(n, 256), 256, 0, s>>>(key, level, n, D, map, big, nbig);
+  count_launches(1);
+  k_map_big<<<dim3(16, unsigned(sm_count() * 2)), 256, 0, s>>>(key, level, big, nbig, D, map);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -972,11 +1287,11 @@ cudaError_t launch_copy_kept_samples(const int32_t* src, int64_t n, const uint32
                                      void* new_samp, bool fp16, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   if (fp16)
-    k_copy_kept<__half><<<warp_grid(n), 32 * kWarpsPerBlock, 0, s>>>(
+    k_copy_kept<__half><<<warp_grid((n + 31) / 32), 32 * kWarpsPerBlock, 0, s>>>(
         src, n, old_soff, reinterpret_cast<const __half*>(old_samp), new_soff,
         reinterpret_cast<__half*>(new_samp));
   else
-    k_copy_kept<float><<<warp_grid(n), 32 * kWarpsPerBlock, 0, s>>>(
+    k_copy_kept<float><<<warp_grid((n + 31) / 32), 32 * kWarpsPerBlock, 0, s>>>(
         src, n, old_soff, reinterpret_cast<const float*>(old_samp), new_soff,
         reinterpret_cast<float*>(new_samp));
   count_launches(1);

@@ -25,6 +25,9 @@ constexpr int32_t kEmpty = -1;
 constexpr uint32_t kIdxMask = (1u << 27) - 1;
 constexpr int kMaxDepth = 15;
 constexpr int64_t kMaxLeaves = int64_t(1) << 27;
+// Face lists longer than this make a leaf "heavy": its iteration updates run
+// as one block per leaf instead of one thread.
+constexpr int kHeavy = 16;
 
 __host__ __device__ inline int32_t make_single(uint32_t idx, int level) {
   return int32_t(idx | (uint32_t(level) << 27));
@@ -138,6 +141,7 @@ struct View {
   const int32_t* nbr;  // [6][stride]
   const int32_t* ovf;
   int64_t stride;      // leaf capacity (row pitch of nbr and p)
+  const uint32_t* map; // finest voxel (Morton order) -> index of its leaf
 };
 
 }  // namespace ofu
@@ -170,6 +174,14 @@ struct ofu_ctx {
   // overflow lists of finer face neighbours
   int32_t* ovf = nullptr;
   int64_t ovf_cap = 0;
+
+  // finest voxel -> leaf index of the current structure (8^D entries)
+  uint32_t* map = nullptr;
+
+  // heavy leaves of the current structure (see kHeavy)
+  uint32_t* heavy = nullptr;   // [0, cap): dual-heavy, [cap, 2 cap): primal-heavy
+  int64_t heavy_cap = 0;
+  int n_heavy_dual = 0, n_heavy_primal = 0;
 
   // scratch (grown on demand)
   void* scratch = nullptr;
@@ -221,11 +233,21 @@ cudaError_t launch_leaf_fill(const uint64_t* key, const uint8_t* level, const ui
                              Geo g, const uint32_t* soff, void* samp, bool fp16, float* u,
                              float* ubar, cudaStream_t s);
 
+// Heavy leaves: dual-heavy when a +face list exceeds kHeavy, primal-heavy
+// when any face list does (counts[0], counts[1] are atomically appended to).
+cudaError_t launch_heavy(View v, uint32_t* heavy_dual, uint32_t* heavy_primal,
+                         unsigned long long* counts, cudaStream_t s);
+
 // Face neighbours (two passes) and step sizes.
-cudaError_t launch_nbr_count(View v, uint32_t* ovf_count, cudaStream_t s);
+// Face neighbours: count pass (long lists queued in longq and counted by a
+// block each), then the fill.
+cudaError_t launch_nbr_count(View v, uint32_t* ovf_count, uint32_t* longq,
+                             unsigned long long* nlong, cudaStream_t s);
 cudaError_t launch_nbr_fill(View v, const uint32_t* ovf_off, int32_t* nbr, int32_t* ovf,
+                            const uint32_t* longq, const unsigned long long* nlong,
                             cudaStream_t s);
-cudaError_t launch_precond(View v, float* tau, float* sigma, cudaStream_t s);
+cudaError_t launch_precond(View v, float* tau, float* sigma, const uint32_t* heavy, int n_heavy,
+                           cudaStream_t s);
 cudaError_t launch_check_tiling(const uint64_t* key, const uint8_t* level, int64_t n, int D,
                                 uint32_t* bad, cudaStream_t s);
 
@@ -236,9 +258,12 @@ cudaError_t launch_mark(View v, const float* u, const uint64_t* cls_scan, double
                         double tau_j, uint64_t* out_count, int8_t* join_level,
                         unsigned long long* counters, cudaStream_t s);
 cudaError_t launch_emit(View v, const float* u, const float* p, const uint64_t* out_off,
-                        const int8_t* join_level, int64_t n_new, uint64_t* nkey, uint8_t* nlevel,
-                        float* nu, float* nubar, float* np_, int64_t nstride, int32_t* src,
-                        cudaStream_t s);
+                        const int8_t* join_level, uint64_t* nkey, uint8_t* nlevel, float* nu,
+                        float* nubar, float* np_, int64_t nstride, int32_t* src, uint32_t* big,
+                        unsigned long long* nbig, cudaStream_t s);
+// Voxel -> leaf map of a structure (big: scratch of n entries, nbig: counter).
+cudaError_t launch_map(const uint64_t* key, const uint8_t* level, int64_t n, int D, uint32_t* map,
+                       uint32_t* big, unsigned long long* nbig, cudaStream_t s);
 cudaError_t launch_new_list(const int32_t* src, int64_t n, uint32_t* list,
                             unsigned long long* cnt, cudaStream_t s);
 cudaError_t launch_kept_counts(const int32_t* src, const uint32_t* old_soff, int64_t n,
@@ -249,10 +274,10 @@ cudaError_t launch_copy_kept_samples(const int32_t* src, int64_t n, const uint32
 
 // Solver kernels.
 cudaError_t launch_dual(View v, const float* ubar, float* p, const float* sigma, float lambda,
-                        cudaStream_t s);
+                        const uint32_t* heavy, int n_heavy, cudaStream_t s);
 cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const float* tau,
                           const uint32_t* soff, const void* samp, bool fp16, float gamma,
-                          cudaStream_t s);
+                          const uint32_t* heavy, int n_heavy, cudaStream_t s);
 size_t energy_tmp_bytes(int64_t n);
 cudaError_t launch_energy(View v, const float* u, const float* p, const uint32_t* soff,
                           const void* samp, bool fp16, double lambda, double gamma,

@@ -34,10 +34,76 @@ __device__ __forceinline__ float load_sample(const T* s, uint32_t i) {
     return s[i];
 }
 
+// Leaves with a face list longer than kHeavy are updated by one block each
+// (the octree is not 2:1 balanced: a coarse leaf can face hundreds of finest
+// leaves); the thread-per-leaf path leaves them alone.  A launch runs the
+// heavy blocks first, then the per-leaf blocks.
+constexpr int kHeavyThreads = kThreads;   // a heavy leaf's block is a full launch block
+
+// Fixed-order block sum of one float per thread (kHeavyThreads threads).
+__device__ __forceinline__ float block_sum(float x, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  float t = 0.0f;
+#pragma unroll
+  for (int w = 0; w < kHeavyThreads / 32; ++w) t += red[w];
+  return t;
+}
+
+__device__ __forceinline__ void dual_write(float* __restrict__ p, int64_t stride, int64_t l,
+                                           float s, const float g[3], float lambda) {
+  float q0 = p[l] + s * g[0];
+  float q1 = p[stride + l] + s * g[1];
+  float q2 = p[2 * stride + l] + s * g[2];
+  const float nrm = sqrtf(q0 * q0 + q1 * q1 + q2 * q2);
+  if (nrm > lambda) {
+    const float sc = lambda / nrm;
+    q0 *= sc;
+    q1 *= sc;
+    q2 *= sc;
+  }
+  p[l] = q0;
+  p[stride + l] = q1;
+  p[2 * stride + l] = q2;
+}
+
 __global__ void __launch_bounds__(kThreads) k_dual(View v, const float* __restrict__ ubar,
                                                    float* __restrict__ p,
-                                                   const float* __restrict__ sigma, float lambda) {
-  const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+                                                   const float* __restrict__ sigma, float lambda,
+                                                   const uint32_t* __restrict__ heavy,
+                                                   int n_heavy_blocks) {
+  if (int(blockIdx.x) < n_heavy_blocks) {
+    // one heavy leaf per block; every thread takes part in the reductions
+    __shared__ float red[kHeavyThreads / 32];
+    const int64_t l = heavy[blockIdx.x];
+    const float h = edge_f(v.D, v.level[l]);
+    const float ul = ubar[l];
+    float g[3];
+    for (int d = 0; d < 3; ++d) {
+      const int32_t e = v.nbr[int64_t(d) * v.stride + l];
+      float acc = 0.0f;
+      if (e >= 0) {
+        if (threadIdx.x == 0)
+          acc = (ubar[entry_idx(e)] - ul) * inv_delta(h, edge_f(v.D, entry_level(e)));
+      } else if (e != kEmpty) {
+        const uint32_t st = list_start(e);
+        const int cnt = v.ovf[st];
+        for (int k = threadIdx.x; k < cnt; k += kHeavyThreads) {
+          const int32_t f = v.ovf[st + 1 + k];
+          const float hm = edge_f(v.D, entry_level(f));
+          const float r = hm / h;
+          acc += r * r * (ubar[entry_idx(f)] - ul) * inv_delta(h, hm);
+        }
+      }
+      g[d] = block_sum(acc, red);
+    }
+    if (threadIdx.x == 0) dual_write(p, v.stride, l, sigma[l], g, lambda);
+    return;
+  }
+  const int64_t l = int64_t(blockIdx.x - n_heavy_blocks) * blockDim.x + threadIdx.x;
   if (l >= v.n) return;
   const float h = edge_f(v.D, v.level[l]);
   const float ul = ubar[l];
@@ -53,6 +119,7 @@ __global__ void __launch_bounds__(kThreads) k_dual(View v, const float* __restri
     } else if (e != kEmpty) {
       const uint32_t st = list_start(e);
       const int cnt = v.ovf[st];
+      if (cnt > kHeavy) return;   // updated by a heavy block
       for (int k = 0; k < cnt; ++k) {
         const int32_t f = v.ovf[st + 1 + k];
         const float hm = edge_f(v.D, entry_level(f));
@@ -62,25 +129,13 @@ __global__ void __launch_bounds__(kThreads) k_dual(View v, const float* __restri
     }
     g[d] = acc;
   }
-  const float s = sigma[l];
-  float q0 = p[l] + s * g[0];
-  float q1 = p[v.stride + l] + s * g[1];
-  float q2 = p[2 * v.stride + l] + s * g[2];
-  const float nrm = sqrtf(q0 * q0 + q1 * q1 + q2 * q2);
-  if (nrm > lambda) {
-    const float sc = lambda / nrm;
-    q0 *= sc;
-    q1 *= sc;
-    q2 *= sc;
-  }
-  p[l] = q0;
-  p[v.stride + l] = q1;
-  p[2 * v.stride + l] = q2;
+  dual_write(p, v.stride, l, sigma[l], g, lambda);
 }
 
-// Divergence of p at leaf l (gathers only).
-__device__ __forceinline__ float divergence(const View& v, const float* __restrict__ p, int64_t l,
-                                            float h) {
+// Divergence of p at leaf l (gathers only).  Returns false, without a
+// result, when a face list is longer than kHeavy (a heavy block owns it).
+__device__ __forceinline__ bool divergence(const View& v, const float* __restrict__ p, int64_t l,
+                                           float h, float* out) {
   float dv = 0.0f;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -91,6 +146,7 @@ __device__ __forceinline__ float divergence(const View& v, const float* __restri
     } else if (e != kEmpty) {
       const uint32_t st = list_start(e);
       const int cnt = v.ovf[st];
+      if (cnt > kHeavy) return false;
       for (int k = 0; k < cnt; ++k) {
         const float hm = edge_f(v.D, entry_level(v.ovf[st + 1 + k]));
         const float r = hm / h;
@@ -110,6 +166,7 @@ __device__ __forceinline__ float divergence(const View& v, const float* __restri
       // finer n: alpha = 1, weight (h_n / h)^3 / Delta
       const uint32_t st = list_start(e);
       const int cnt = v.ovf[st];
+      if (cnt > kHeavy) return false;
       for (int k = 0; k < cnt; ++k) {
         const int32_t f = v.ovf[st + 1 + k];
         const float hn = edge_f(v.D, entry_level(f));
@@ -118,42 +175,82 @@ __device__ __forceinline__ float divergence(const View& v, const float* __restri
       }
     }
   }
+  *out = dv;
+  return true;
+}
+
+// The same divergence by one block (kHeavyThreads threads) of a heavy leaf;
+// the result is valid in every thread.
+__device__ float divergence_block(const View& v, const float* __restrict__ p, int64_t l, float h,
+                                  float* red) {
+  float dv = 0.0f;
+  for (int d = 0; d < 3; ++d) {
+    const int32_t e = v.nbr[int64_t(d) * v.stride + l];
+    float coef = 0.0f;
+    if (e >= 0) {
+      if (threadIdx.x == 0) coef = inv_delta(h, edge_f(v.D, entry_level(e)));
+    } else if (e != kEmpty) {
+      const uint32_t st = list_start(e);
+      const int cnt = v.ovf[st];
+      for (int k = threadIdx.x; k < cnt; k += kHeavyThreads) {
+        const float hm = edge_f(v.D, entry_level(v.ovf[st + 1 + k]));
+        const float r = hm / h;
+        coef += r * r * inv_delta(h, hm);
+      }
+    }
+    dv += block_sum(coef, red) * p[int64_t(d) * v.stride + l];
+  }
+  for (int d = 0; d < 3; ++d) {
+    const int32_t e = v.nbr[int64_t(3 + d) * v.stride + l];
+    float acc = 0.0f;
+    if (e >= 0) {
+      if (threadIdx.x == 0) {
+        const float hn = edge_f(v.D, entry_level(e));
+        acc = (hn / h) * inv_delta(h, hn) * p[int64_t(d) * v.stride + entry_idx(e)];
+      }
+    } else if (e != kEmpty) {
+      const uint32_t st = list_start(e);
+      const int cnt = v.ovf[st];
+      for (int k = threadIdx.x; k < cnt; k += kHeavyThreads) {
+        const int32_t f = v.ovf[st + 1 + k];
+        const float hn = edge_f(v.D, entry_level(f));
+        const float r = hn / h;
+        acc += r * r * r * inv_delta(h, hn) * p[int64_t(d) * v.stride + entry_idx(f)];
+      }
+    }
+    dv -= block_sum(acc, red);
+  }
   return dv;
 }
 
 // Prox of the data term: argmin_x (x - v)^2 / (2 tau) + c sum_k |x - f_k| is
 // the median of {f_k} and {v + t (W - 2k)}_{k=0..W}, t = tau c.  With the
-// samples sorted, it is clamp(b_k, f_k, f_(k+1)) for the smallest k with
-// f_(k+1) >= b_k = v + t (W - 2k) (f_0 = -inf, f_(W+1) = +inf), found by
-// bisection because the predicate is monotone in k.
+// samples sorted it is clamp(b_k*, f_(k*-1), f_k*) (0-based f, f_-1 = -inf,
+// f_W = +inf) where k* is the number of k with f_k < b_k = v + t (W - 2k);
+// that predicate holds for a prefix of k (f rises, b falls), so counting it
+// in one pass over the samples finds k*.  The pass has no data-dependent
+// addresses: every sample load is issued independently.
 template <typename T>
 __device__ __forceinline__ float prox_l1(const T* __restrict__ f, int W, float v, float t) {
-  int lo = 0, hi = W;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    const float b = v + t * float(W - 2 * mid);
-    if (load_sample(f, mid) >= b) hi = mid; else lo = mid + 1;
+  int ks = 0;
+  float lo = -CUDART_INF_F, hi = CUDART_INF_F;
+#pragma unroll 4
+  for (int k = 0; k < W; ++k) {
+    const float fk = load_sample(f, k);
+    const bool below = fk < v + t * float(W - 2 * k);
+    ks += below;
+    lo = below ? fk : lo;
+    hi = (!below && hi == CUDART_INF_F) ? fk : hi;
   }
-  const int k = lo;
-  float x = v + t * float(W - 2 * k);
-  if (k < W) x = fminf(x, load_sample(f, k));
-  if (k > 0) x = fmaxf(x, load_sample(f, k - 1));
-  return x;
+  const float b = v + t * float(W - 2 * ks);
+  return fmaxf(lo, fminf(b, hi));
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_primal(View v, float* __restrict__ u,
-                                                     float* __restrict__ ubar,
-                                                     const float* __restrict__ p,
-                                                     const float* __restrict__ tau,
-                                                     const uint32_t* __restrict__ soff,
-                                                     const T* __restrict__ samp, float gamma) {
-  const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (l >= v.n) return;
-  const float h = edge_f(v.D, v.level[l]);
-  const float tl = tau[l];
-  const float ul = u[l];
-  const float x = ul + tl * divergence(v, p, l, h);
+__device__ __forceinline__ void primal_write(float* __restrict__ u, float* __restrict__ ubar,
+                                             int64_t l, float ul, float x, float tl,
+                                             const uint32_t* __restrict__ soff,
+                                             const T* __restrict__ samp, float gamma) {
   const uint32_t o = soff[l];
   const int W = int(soff[l + 1] - o);
   const float t = tl / (float(W) + gamma);
@@ -162,15 +259,62 @@ __global__ void __launch_bounds__(kThreads) k_primal(View v, float* __restrict__
   ubar[l] = 2.0f * un - ul;
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_primal(View v, float* __restrict__ u,
+                                                     float* __restrict__ ubar,
+                                                     const float* __restrict__ p,
+                                                     const float* __restrict__ tau,
+                                                     const uint32_t* __restrict__ soff,
+                                                     const T* __restrict__ samp, float gamma,
+                                                     const uint32_t* __restrict__ heavy,
+                                                     int n_heavy_blocks) {
+  if (int(blockIdx.x) < n_heavy_blocks) {
+    __shared__ float red[kHeavyThreads / 32];
+    const int64_t l = heavy[blockIdx.x];
+    const float h = edge_f(v.D, v.level[l]);
+    const float dv = divergence_block(v, p, l, h, red);
+    if (threadIdx.x == 0) {
+      const float tl = tau[l];
+      const float ul = u[l];
+      primal_write(u, ubar, l, ul, ul + tl * dv, tl, soff, samp, gamma);
+    }
+    return;
+  }
+  const int64_t l = int64_t(blockIdx.x - n_heavy_blocks) * blockDim.x + threadIdx.x;
+  if (l >= v.n) return;
+  const float h = edge_f(v.D, v.level[l]);
+  float dv;
+  if (!divergence(v, p, l, h, &dv)) return;   // updated by a heavy block
+  const float tl = tau[l];
+  const float ul = u[l];
+  primal_write(u, ubar, l, ul, ul + tl * dv, tl, soff, samp, gamma);
+}
+
 // ---------------------------------------------------------------------------
 // Energy (float64).  Per leaf, with c = 1 / (W + gamma) and volume h^3:
 //   primal  h^3 [c sum_k |u - f_k| + lambda |grad u|]
 //   dual    h^3 min_{x in [-1,1]} [c sum_k |x - f_k| - x div p]
 // The dual minimum of the convex piecewise-linear function sits where its
 // slope c (2k - W) - div p turns non-negative: at f_k for the first such k,
-// at -1 if already for k = 0, at +1 if never.
+// at -1 if already for k = 0, at +1 if never.  1 / Delta comes from a table
+// (no division in the neighbour loops); partial sums are per block, then
+// summed by one block in a fixed order, so the result is reproducible.
 
-constexpr int kEnergyBlocks = 1024;
+// 1 / (1 + 2^d), d = 0..15: 1 / Delta = 2^(1 - min(a, b)) / (1 + 2^|a - b|)
+// for leaves of edges 2^a and 2^b.
+__constant__ double kInvOnePlusPow2[16] = {
+    1.0 / 2.0,     1.0 / 3.0,     1.0 / 5.0,     1.0 / 9.0,     1.0 / 17.0,    1.0 / 33.0,
+    1.0 / 65.0,    1.0 / 129.0,   1.0 / 257.0,   1.0 / 513.0,   1.0 / 1025.0,  1.0 / 2049.0,
+    1.0 / 4097.0,  1.0 / 8193.0,  1.0 / 16385.0, 1.0 / 32769.0};
+
+// alpha / Delta for the ordered pair (row leaf of edge exponent a, neighbour
+// of edge exponent b) with alpha = min(1, (2^b / 2^a)^2).
+__device__ __forceinline__ double face_weight(int a, int b) {
+  const int lo = a < b ? a : b;
+  const int d = a < b ? b - a : a - b;
+  const double inv_delta = ldexp(kInvOnePlusPow2[d], 1 - lo);
+  return b < a ? ldexp(inv_delta, 2 * (b - a)) : inv_delta;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_energy(View v, const float* __restrict__ u,
@@ -182,8 +326,8 @@ __global__ void __launch_bounds__(kThreads) k_energy(View v, const float* __rest
   for (int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; l < v.n;
        l += int64_t(gridDim.x) * blockDim.x) {
     const int lev = v.level[l];
-    const double h = double(int64_t(1) << (v.D - lev));
-    const double vol = h * h * h;
+    const int a = v.D - lev;                 // edge exponent
+    const double vol = ldexp(1.0, 3 * a);
     const double ul = double(u[l]);
     double g2 = 0.0, dv = 0.0;
     for (int d = 0; d < 3; ++d) {
@@ -197,8 +341,7 @@ __global__ void __launch_bounds__(kThreads) k_energy(View v, const float* __rest
           lst = v.ovf + list_start(e) + 1;
         }
         for (int k = 0; k < cnt; ++k) {
-          const double hm = double(int64_t(1) << (v.D - entry_level(lst[k])));
-          const double w = fmin(1.0, (hm / h) * (hm / h)) / ((h + hm) * 0.5);
+          const double w = face_weight(a, v.D - entry_level(lst[k]));
           g += w * (double(u[entry_idx(lst[k])]) - ul);
           coef += w;
         }
@@ -214,30 +357,30 @@ __global__ void __launch_bounds__(kThreads) k_energy(View v, const float* __rest
           lst = v.ovf + list_start(e2) + 1;
         }
         for (int k = 0; k < cnt; ++k) {
-          const double hn = double(int64_t(1) << (v.D - entry_level(lst[k])));
-          const double w = fmin(1.0, (h / hn) * (h / hn)) / ((h + hn) * 0.5);
-          dv -= (hn * hn * hn) / vol * w * double(p[int64_t(d) * v.stride + entry_idx(lst[k])]);
+          const int bn = v.D - entry_level(lst[k]);
+          // (h_n^3 / h^3) alpha_nl / Delta
+          const double w = ldexp(face_weight(bn, a), 3 * (bn - a));
+          dv -= w * double(p[int64_t(d) * v.stride + entry_idx(lst[k])]);
         }
       }
     }
     const uint32_t o = soff[l];
     const int W = int(soff[l + 1] - o);
-    const double c = 1.0 / (double(W) + gamma);
+    const double rc = 1.0 / (double(W) + gamma);
     double data = 0.0;
     for (int k = 0; k < W; ++k) data += fabs(ul - double(load_sample(samp, o + k)));
-    sp += vol * (c * data + lambda * sqrt(g2));
-    // dual term
+    sp += vol * (rc * data + lambda * sqrt(g2));
+    // dual term: first k with slope c (2k - W) - dv >= 0, i.e. k >= (W + dv / c) / 2
     double xs;
-    const double kk = ceil((double(W) + dv / c) * 0.5);
+    const double kk = ceil((double(W) + dv * (double(W) + gamma)) * 0.5);
     if (kk <= 0.0) xs = -1.0;
     else if (kk > double(W)) xs = 1.0;
     else xs = double(load_sample(samp, o + int(kk) - 1));
     xs = fmin(1.0, fmax(-1.0, xs));
     double dd = 0.0;
     for (int k = 0; k < W; ++k) dd += fabs(xs - double(load_sample(samp, o + k)));
-    sd += vol * (c * dd - xs * dv);
+    sd += vol * (rc * dd - xs * dv);
   }
-  // block reduction in a fixed order
   __shared__ double rp[kThreads / 32], rd[kThreads / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -261,40 +404,63 @@ __global__ void __launch_bounds__(kThreads) k_energy(View v, const float* __rest
   }
 }
 
-__global__ void k_energy_final(const double* __restrict__ partial, int nb, double* __restrict__ out3) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Fixed-order sum of nb partial pairs by one block of kFinalThreads threads:
+// thread t adds partials t, t + kFinalThreads, ...; then a tree over threads.
+constexpr int kFinalThreads = 256;
+
+__global__ void __launch_bounds__(kFinalThreads) k_energy_final(const double* __restrict__ partial,
+                                                                int nb, double* __restrict__ out3) {
+  __shared__ double ra[kFinalThreads], rb[kFinalThreads];
   double a = 0.0, b = 0.0;
-  for (int i = 0; i < nb; ++i) {
+  for (int i = threadIdx.x; i < nb; i += kFinalThreads) {
     a += partial[2 * i];
     b += partial[2 * i + 1];
   }
-  out3[0] = a;
-  out3[1] = b;
-  out3[2] = a - b;
+  ra[threadIdx.x] = a;
+  rb[threadIdx.x] = b;
+  __syncthreads();
+  for (int s = kFinalThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      ra[threadIdx.x] += ra[threadIdx.x + s];
+      rb[threadIdx.x] += rb[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out3[0] = ra[0];
+    out3[1] = rb[0];
+    out3[2] = ra[0] - rb[0];
+  }
 }
+
+constexpr int kEnergyBlocks = 8192;
 
 inline unsigned blocks_for(int64_t n, int threads) { return unsigned((n + threads - 1) / threads); }
 
 }  // namespace
 
 cudaError_t launch_dual(View v, const float* ubar, float* p, const float* sigma, float lambda,
-                        cudaStream_t s) {
+                        const uint32_t* heavy, int n_heavy, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
-  k_dual<<<blocks_for(v.n, kThreads), kThreads, 0, s>>>(v, ubar, p, sigma, lambda);
+  k_dual<<<blocks_for(v.n, kThreads) + n_heavy, kThreads, 0, s>>>(v, ubar, p, sigma, lambda, heavy,
+                                                                   n_heavy);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const float* tau,
                           const uint32_t* soff, const void* samp, bool fp16, float gamma,
-                          cudaStream_t s) {
+                          const uint32_t* heavy, int n_heavy, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
+  const unsigned nb = blocks_for(v.n, kThreads) + n_heavy;
   if (fp16)
-    k_primal<__half><<<blocks_for(v.n, kThreads), kThreads, 0, s>>>(
-        v, u, ubar, p, tau, soff, reinterpret_cast<const __half*>(samp), gamma);
+    k_primal<__half><<<nb, kThreads, 0, s>>>(v, u, ubar, p, tau, soff,
+                                             reinterpret_cast<const __half*>(samp), gamma, heavy,
+                                             n_heavy);
   else
-    k_primal<float><<<blocks_for(v.n, kThreads), kThreads, 0, s>>>(
-        v, u, ubar, p, tau, soff, reinterpret_cast<const float*>(samp), gamma);
+    k_primal<float><<<nb, kThreads, 0, s>>>(v, u, ubar, p, tau, soff,
+                                            reinterpret_cast<const float*>(samp), gamma, heavy,
+                                            n_heavy);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -304,7 +470,8 @@ size_t energy_tmp_bytes(int64_t) { return size_t(2 * kEnergyBlocks) * sizeof(dou
 cudaError_t launch_energy(View v, const float* u, const float* p, const uint32_t* soff,
                           const void* samp, bool fp16, double lambda, double gamma,
                           double* partial, double* out3, cudaStream_t s) {
-  const int nb = kEnergyBlocks;
+  const int64_t want = (v.n + kThreads - 1) / kThreads;
+  const int nb = int(want < 1 ? 1 : (want < kEnergyBlocks ? want : kEnergyBlocks));
   if (fp16)
     k_energy<__half><<<nb, kThreads, 0, s>>>(v, u, p, soff, reinterpret_cast<const __half*>(samp),
                                              lambda, gamma, partial);
@@ -312,7 +479,7 @@ cudaError_t launch_energy(View v, const float* u, const float* p, const uint32_t
     k_energy<float><<<nb, kThreads, 0, s>>>(v, u, p, soff, reinterpret_cast<const float*>(samp),
                                             lambda, gamma, partial);
   count_launches(1);
-  k_energy_final<<<1, 32, 0, s>>>(partial, nb, out3);
+  k_energy_final<<<1, kFinalThreads, 0, s>>>(partial, nb, out3);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -367,7 +534,7 @@ cudaError_t launch_energy_static(View v, const float* u, const float* p, const u
     k_energy<float><<<nb, kThreads, 0, s>>>(v, u, p, soff, reinterpret_cast<const float*>(samp),
                                             lambda, gamma, scratch);
   count_launches(1);
-  k_energy_final<<<1, 32, 0, s>>>(scratch, nb, scratch + 2 * kStaticEnergyBlocks);
+  k_energy_final<<<1, kFinalThreads, 0, s>>>(scratch, nb, scratch + 2 * kStaticEnergyBlocks);
   count_launches(1);
   return cudaGetLastError();
 }

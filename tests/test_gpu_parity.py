@@ -14,6 +14,9 @@ pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarnin
 # fixed structure, so after k iterations the difference is below ~k * 1e-7.
 TOL_STEP = 1e-5        # up to ~30 iterations
 TOL_FINAL = 1e-4       # after the workload's iteration count
+# Step sizes are float32 sums of up to ~6 x 64 terms (long finer-neighbour
+# lists): relative rounding error up to a few hundred x 2^-24 ~ 2e-5.
+TOL_STEPSIZE = 2e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -74,8 +77,8 @@ def test_construction_samples_neighbours_steps(name, kw):
     # median init: float64 median rounded once to float32
     np.testing.assert_array_equal(u, st.u.astype(np.float32))
     assert_same_neighbours(o, st)
-    np.testing.assert_allclose(o.field(octfuse.FIELD_TAU), st.tau, rtol=1e-6)
-    np.testing.assert_allclose(o.field(octfuse.FIELD_SIGMA), st.sigma, rtol=1e-6)
+    np.testing.assert_allclose(o.field(octfuse.FIELD_TAU), st.tau, rtol=TOL_STEPSIZE)
+    np.testing.assert_allclose(o.field(octfuse.FIELD_SIGMA), st.sigma, rtol=TOL_STEPSIZE)
     assert len(k) % 256 != 0 or True   # sizes are ragged with respect to the block size
 
 
@@ -136,7 +139,7 @@ def test_lockstep_sphere_workload():
         changes += ns + nj
         if done in (10, 100):
             assert_same_neighbours(o, st)
-            np.testing.assert_allclose(o.field(octfuse.FIELD_TAU), st.tau, rtol=1e-6)
+            np.testing.assert_allclose(o.field(octfuse.FIELD_TAU), st.tau, rtol=TOL_STEPSIZE)
         np.testing.assert_allclose(o.field(octfuse.FIELD_U), st.u, atol=1e-6)
     assert changes > 0
     np.testing.assert_allclose(o.field(octfuse.FIELD_U), st.u, atol=TOL_FINAL)
@@ -151,8 +154,8 @@ def test_random_octrees_imported():
         st = solver.initial_state(scene, k, lv)
         assert_same_neighbours(o, st)
         np.testing.assert_array_equal(o.field(octfuse.FIELD_W), st.W)
-        np.testing.assert_allclose(o.field(octfuse.FIELD_TAU), st.tau, rtol=1e-6)
-        np.testing.assert_allclose(o.field(octfuse.FIELD_SIGMA), st.sigma, rtol=1e-6)
+        np.testing.assert_allclose(o.field(octfuse.FIELD_TAU), st.tau, rtol=TOL_STEPSIZE)
+        np.testing.assert_allclose(o.field(octfuse.FIELD_SIGMA), st.sigma, rtol=TOL_STEPSIZE)
         o.iterate(15)
         solver.step(st, 15)
         np.testing.assert_allclose(o.field(octfuse.FIELD_U), st.u, atol=TOL_STEP)
@@ -322,7 +325,7 @@ def test_full_size_one_iteration_and_energy(full):
                       u=None, ubar=None, p=None, lam=scene.lam, gamma=scene.gamma)
     st.rebuild_operators()
     assert_same_neighbours(o, st)
-    np.testing.assert_allclose(o.field(octfuse.FIELD_TAU), st.tau, rtol=1e-6)
+    np.testing.assert_allclose(o.field(octfuse.FIELD_TAU), st.tau, rtol=TOL_STEPSIZE)
     sync_oracle(st, o)
     P, D, G = o.energy()
     Po, Do, _ = solver.energies(st)
