@@ -56,6 +56,7 @@ def args_():
     ap.add_argument("--iters", type=int, default=0, help="override the workload's iteration count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-tte", action="store_true", help="skip the time-to-energy measurement")
     return ap.parse_args()
 
 
@@ -214,6 +215,47 @@ def peak_hbm():
         return 6800.0, "fallback"
 
 
+def time_to_energy(a, scene, of, stream, depth_d, intr_d, pose_d):
+    """Reference energy E* = primal energy of the plain float32 solve at the
+    workload's iteration count; then, per form, the device time (from the
+    frames, construction included) and iterations until the primal energy
+    first drops to E* (1 + 1e-4), checked after every restructure window."""
+    import torch
+    F, H, W = scene.depth.shape
+    R = scene.restructure_every
+    iters = a.iters or scene.iters
+
+    def ctx_for(fp16):
+        c = of.ofu_create_octree(of.params_for(scene, sample_fp16=fp16), stream.cuda_stream)
+        of.ofu_integrate_frames(c, F, H, W, depth_d.data_ptr(), intr_d.data_ptr(), pose_d.data_ptr())
+        return c
+
+    c = ctx_for(False)
+    done, li, (Pr, Dr, Gr) = of.ofu_solve(c, iters, R, 0, 0.0)
+    of.ofu_destroy(c)
+    target = Pr * (1 + 1e-4)
+    out = {"reference": f"plain float32 energy after {iters} iterations", "reference_energy": Pr,
+           "reference_gap": Gr, "target": target, "check_every": R}
+    for name, fp16 in (("plain_f32", False), ("f16_samples", True)):
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        c = ctx_for(fp16)
+        it, reached, P = 0, False, float("inf")
+        while it < 4 * iters:
+            _, _, (P, _, _) = of.ofu_solve(c, R, 0, R, 0.0)
+            it += R
+            if P <= target:
+                reached = True
+                break
+            of.ofu_restructure(c)
+        ev1.record(stream)
+        ev1.synchronize()
+        out[name] = {"ms": ev0.elapsed_time(ev1), "iters": it, "reached": reached, "energy": P}
+        of.ofu_destroy(c)
+    return out
+
+
 def main():
     a = args_()
     rank = int(os.environ.get("RANK", "0"))
@@ -256,9 +298,12 @@ def main():
     ctx = of.ofu_create_octree(of.params_for(scene, sample_fp16=a.fp16), stream.cuda_stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    s0s = []
+
     def step():
         of.ofu_integrate_frames(ctx, F, H, W, depth_d.data_ptr(), intr_d.data_ptr(), pose_d.data_ptr())
         n0 = of.ofu_num_leaves(ctx)
+        s0s.append(of.ofu_export_field(ctx, of.FIELD_SAMPLES, None, 0))
         done, li, e = of.ofu_solve(ctx, iters, R, 0, 0.0)
         return n0, li, e
 
@@ -353,6 +398,8 @@ def main():
                       if ms[1 - dom] > 0 else 0.0, "avg_launch_us": 1e3 * ms[1 - dom] / max(nl[1 - dom], 1)},
             "iteration_share_of_step": (ms[0] + ms[1]) / sum(times)}
 
+    tte = None if a.no_tte else time_to_energy(a, scene, of, stream, depth_d, intr_d, pose_d)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         rate, nleaf, it, dt, setup = cpu_rate(scene, a.cpu_seconds)
@@ -368,11 +415,12 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f16-samples/f32" if a.fp16 else "f32",
             "data": "synthetic", "config": config_of(a, scene, extra={
                 "leaves_initial": int(statistics.median(n0s)), "leaves_final": n_final,
+                "samples_initial": int(statistics.median(s0s)),
                 "samples_final": n_samples, "final_energy": energies}),
             "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
-            "roofline": roof, "clocks": clk, "cpu_baseline": cpu,
+            "roofline": roof, "clocks": clk, "cpu_baseline": cpu, "time_to_energy": tte,
         }
         print(json.dumps(line), flush=True)
     of.ofu_destroy(ctx)
