@@ -225,9 +225,18 @@ def time_to_energy(a, scene, of, stream, depth_d, intr_d, pose_d):
     R = scene.restructure_every
     iters = a.iters or scene.iters
 
-    def ctx_for(fp16):
+    from paper_1608_07411_gb300 import warm_start
+    try:
+        net = of.ofu_mlp_create(stream.cuda_stream)
+        of.ofu_mlp_set_params(net, warm_start.load_params())
+    except (OSError, ValueError):
+        net = None
+
+    def ctx_for(fp16, warm=False):
         c = of.ofu_create_octree(of.params_for(scene, sample_fp16=fp16), stream.cuda_stream)
         of.ofu_integrate_frames(c, F, H, W, depth_d.data_ptr(), intr_d.data_ptr(), pose_d.data_ptr())
+        if warm:
+            of.ofu_warm_start(c, net)
         return c
 
     c = ctx_for(False)
@@ -236,11 +245,14 @@ def time_to_energy(a, scene, of, stream, depth_d, intr_d, pose_d):
     target = Pr * (1 + 1e-4)
     out = {"reference": f"plain float32 energy after {iters} iterations", "reference_energy": Pr,
            "reference_gap": Gr, "target": target, "check_every": R}
-    for name, fp16 in (("plain_f32", False), ("f16_samples", True)):
+    forms = [("plain_f32", False, False), ("f16_samples", True, False)]
+    if net is not None:
+        forms += [("f32_warm_start", False, True), ("f16_warm_start", True, True)]
+    for name, fp16, warm in forms:
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        c = ctx_for(fp16)
+        c = ctx_for(fp16, warm)
         it, reached, P = 0, False, float("inf")
         while it < 4 * iters:
             _, _, (P, _, _) = of.ofu_solve(c, R, 0, R, 0.0)
@@ -253,6 +265,8 @@ def time_to_energy(a, scene, of, stream, depth_d, intr_d, pose_d):
         ev1.synchronize()
         out[name] = {"ms": ev0.elapsed_time(ev1), "iters": it, "reached": reached, "energy": P}
         of.ofu_destroy(c)
+    if net is not None:
+        of.ofu_mlp_destroy(net)
     return out
 
 

@@ -194,6 +194,73 @@ ofu_status ofu_import_leaves(ofu_ctx* ctx, const uint64_t* keys, const uint8_t* 
  * may be NULL for ubar = u) on the current structure. */
 ofu_status ofu_set_state(ofu_ctx* ctx, const float* u, const float* ubar, const float* p, int64_t n);
 
+/* ---- learned warm start (not in the paper) ----------------------------- */
+/*
+ * A per-leaf network replaces the median initialisation of observed leaves
+ * by a learned initial u.  The paper has no learned component; its
+ * initialisation is the plain per-point data (Sec. 3.1).
+ *
+ * Features, 39 float32 per leaf (row-major [N][39]):
+ *   x[0..31]  nearest-rank quantiles f_(r_j) of the leaf's sorted samples,
+ *             r_j = ceil((2j - 1) W / 64) for j = 1..32 (0 when W = 0);
+ *   x[32]     level / max_depth;
+ *   x[33..38] per face (+x, +y, +z, -x, -y, -z) the mean of the neighbours'
+ *             current u weighted by the share of the face each covers,
+ *             min(1, (h_m / h_l)^2); the leaf's own u on the domain boundary.
+ * Network: h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = tanh(w3 . h2 + b3),
+ * W1 [64][39], W2 [64][64]; the 6785 float32 parameters are packed in the
+ * order W1, b1, W2, b2, w3, b3 (row-major).
+ * Training loss over a batch: sum_i w_i (y_i - t_i)^2 / sum_i w_i; Adam with
+ * beta1 = 0.9, beta2 = 0.999, eps = 1e-8 and bias correction. */
+typedef struct ofu_mlp ofu_mlp;
+
+/* Number of packed parameters (6785). */
+int64_t ofu_mlp_num_params(void);
+
+/* Creates a network with all parameters 0 on the current device; work runs
+ * on `cuda_stream`.  ofu_last_error(NULL) describes a failure. */
+ofu_status ofu_mlp_create(void* cuda_stream, ofu_mlp** out);
+void ofu_mlp_destroy(ofu_mlp* net);
+const char* ofu_mlp_last_error(const ofu_mlp* net);
+
+/* Copies the packed parameters in (host or device; resets Adam's moments and
+ * step count) or out.  Synchronise the network's stream. */
+ofu_status ofu_mlp_set_params(ofu_mlp* net, const float* params);
+ofu_status ofu_mlp_get_params(ofu_mlp* net, float* params);
+
+/* y[B] = network(X[B][39]); device pointers; asynchronous. */
+ofu_status ofu_mlp_forward(ofu_mlp* net, const float* X, int64_t B, float* y);
+
+/* Gradient of the batch loss with respect to the packed parameters and the
+ * loss itself.  X [*][39], t [*], w [*] are device arrays; `rows` (device,
+ * int32 [B], may be NULL for rows 0..B-1) selects the batch.  `grad` (host or
+ * device, 6785 floats) and `loss` (host) may be NULL.  Per-block partial
+ * gradients are summed in a fixed order, so results are reproducible.
+ * Synchronises the network's stream. */
+ofu_status ofu_mlp_gradient(ofu_mlp* net, const float* X, const float* t, const float* w,
+                            const int32_t* rows, int64_t B, float* grad, double* loss);
+
+/* One Adam step (learning rate lr > 0) on the batch's gradient.  With a
+ * non-NULL `loss` (host) the batch loss before the step is returned and the
+ * stream is synchronised; otherwise the call is asynchronous. */
+ofu_status ofu_mlp_train_step(ofu_mlp* net, const float* X, const float* t, const float* w,
+                              const int32_t* rows, int64_t B, float lr, double* loss);
+
+/* Features of the current leaves from the current u into X (device, at
+ * least cap_rows >= N rows of 39 floats); asynchronous. */
+ofu_status ofu_features(ofu_ctx* ctx, float* X, int64_t cap_rows);
+
+/* Warm start: u = ubar = network(features) for leaves with W > 0 whose
+ * output is finite; other leaves keep their value (the median, -1 where
+ * unobserved).  Features are taken from the current u, so call it right after
+ * ofu_integrate_frames.  The dual variable is started consistently with the
+ * new field: p = lambda grad u / |grad u| where |grad u| >= 0.05 (truncation
+ * units per finest voxel; a TSDF ramp has 1/4 at delta = 4 voxels), p = 0
+ * elsewhere -- the optimal dual wherever the field has an edge.  With p = 0
+ * the first primal steps would pull u back towards the median.  Asynchronous
+ * on the context's stream (it first waits for the network's stream). */
+ofu_status ofu_warm_start(ofu_ctx* ctx, const ofu_mlp* net);
+
 /* ---- allocation-free variant -------------------------------------------- */
 
 /* ofu_energy for callers that must not cause a device allocation: a caller

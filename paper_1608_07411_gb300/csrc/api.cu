@@ -758,6 +758,197 @@ ofu_status ofu_energy_static(ofu_ctx* ctx, double* out3) {
   return OFU_OK;
 }
 
+// ---- warm-start network ----------------------------------------------------
+
+#define MCU(call)                                                        \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) {                                             \
+      net->poisoned = true;                                              \
+      net->err = std::string(#call) + ": " + cudaGetErrorString(e_);     \
+      cudaGetLastError();                                                \
+      return e_ == cudaErrorMemoryAllocation ? OFU_ENOMEM : OFU_ECUDA;   \
+    }                                                                    \
+  } while (0)
+
+// Gradient magnitude (truncation units per finest voxel) above which the
+// warm start sets p to lambda times the field's normal: the true TSDF ramps
+// at 1/delta = 1/4 per voxel, prediction noise on flat regions stays far below.
+constexpr float kWarmEdge = 0.05f;
+
+static ofu_status mlp_ready(ofu_mlp* net) {
+  if (!net) return OFU_EINVAL;
+  if (net->poisoned) {
+    net->err = "network object poisoned by an earlier CUDA error";
+    return OFU_ESTATE;
+  }
+  return OFU_OK;
+}
+
+static ofu_status mlp_partials(ofu_mlp* net, int64_t B) {
+  const int64_t nb = mlp_grad_blocks(B);
+  if (nb <= net->partial_blocks) return OFU_OK;
+  if (net->partial) MCU(cudaFree(net->partial));
+  if (net->sums) MCU(cudaFree(net->sums));
+  net->partial = nullptr;
+  net->sums = nullptr;
+  net->partial_blocks = 0;
+  MCU(cudaMalloc(&net->partial, size_t(nb) * kMlpParams * sizeof(float)));
+  MCU(cudaMalloc(&net->sums, (2 * size_t(nb) + 2) * sizeof(double)));
+  net->partial_blocks = nb;
+  return OFU_OK;
+}
+
+int64_t ofu_mlp_num_params(void) { return kMlpParams; }
+
+ofu_status ofu_mlp_create(void* cuda_stream, ofu_mlp** out) {
+  if (!out) return OFU_EINVAL;
+  *out = nullptr;
+  ofu_mlp* net = new ofu_mlp();
+  net->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  const size_t pb = size_t(kMlpParams) * sizeof(float);
+  cudaError_t e = cudaMalloc(&net->params, pb);
+  if (e == cudaSuccess) e = cudaMalloc(&net->m, pb);
+  if (e == cudaSuccess) e = cudaMalloc(&net->v, pb);
+  if (e == cudaSuccess) e = cudaMalloc(&net->grad, pb);
+  if (e == cudaSuccess) e = cudaMallocHost(&net->pinned, 64);
+  if (e == cudaSuccess) e = cudaMemsetAsync(net->params, 0, pb, net->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(net->m, 0, pb, net->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(net->v, 0, pb, net->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("ofu_mlp_create: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    ofu_mlp_destroy(net);
+    return e == cudaErrorMemoryAllocation ? OFU_ENOMEM : OFU_ECUDA;
+  }
+  *out = net;
+  return OFU_OK;
+}
+
+void ofu_mlp_destroy(ofu_mlp* net) {
+  if (!net) return;
+  cudaStreamSynchronize(net->stream);
+  cudaFree(net->params);
+  cudaFree(net->m);
+  cudaFree(net->v);
+  cudaFree(net->grad);
+  cudaFree(net->partial);
+  cudaFree(net->sums);
+  if (net->pinned) cudaFreeHost(net->pinned);
+  cudaGetLastError();
+  delete net;
+}
+
+const char* ofu_mlp_last_error(const ofu_mlp* net) { return net ? net->err.c_str() : g_create_error.c_str(); }
+
+ofu_status ofu_mlp_set_params(ofu_mlp* net, const float* params) {
+  ST(mlp_ready(net));
+  if (!params) {
+    net->err = "set_params: params is NULL";
+    return OFU_EINVAL;
+  }
+  const size_t pb = size_t(kMlpParams) * sizeof(float);
+  MCU(cudaMemcpyAsync(net->params, params, pb, cudaMemcpyDefault, net->stream));
+  MCU(cudaMemsetAsync(net->m, 0, pb, net->stream));
+  MCU(cudaMemsetAsync(net->v, 0, pb, net->stream));
+  MCU(cudaStreamSynchronize(net->stream));
+  net->step = 0;
+  return OFU_OK;
+}
+
+ofu_status ofu_mlp_get_params(ofu_mlp* net, float* params) {
+  ST(mlp_ready(net));
+  if (!params) {
+    net->err = "get_params: params is NULL";
+    return OFU_EINVAL;
+  }
+  MCU(cudaMemcpyAsync(params, net->params, size_t(kMlpParams) * sizeof(float), cudaMemcpyDefault,
+                      net->stream));
+  MCU(cudaStreamSynchronize(net->stream));
+  return OFU_OK;
+}
+
+ofu_status ofu_mlp_forward(ofu_mlp* net, const float* X, int64_t B, float* y) {
+  ST(mlp_ready(net));
+  if (B < 0 || (B > 0 && (!X || !y))) {
+    net->err = "forward: need B >= 0 and device X, y";
+    return OFU_EINVAL;
+  }
+  MCU(launch_mlp_forward(net->params, X, B, y, net->stream));
+  return OFU_OK;
+}
+
+static ofu_status mlp_grad(ofu_mlp* net, const float* X, const float* t, const float* w,
+                           const int32_t* rows, int64_t B) {
+  if (B < 1 || !X || !t || !w) {
+    net->err = "gradient: need B >= 1 and device X, t, w";
+    return OFU_EINVAL;
+  }
+  ST(mlp_partials(net, B));
+  MCU(launch_mlp_grad(net->params, X, t, w, rows, B, net->partial, net->sums, net->grad,
+                      net->sums + 2 * net->partial_blocks, net->stream));
+  return OFU_OK;
+}
+
+ofu_status ofu_mlp_gradient(ofu_mlp* net, const float* X, const float* t, const float* w,
+                            const int32_t* rows, int64_t B, float* grad, double* loss) {
+  ST(mlp_ready(net));
+  ST(mlp_grad(net, X, t, w, rows, B));
+  if (grad)
+    MCU(cudaMemcpyAsync(grad, net->grad, size_t(kMlpParams) * sizeof(float), cudaMemcpyDefault,
+                        net->stream));
+  MCU(cudaMemcpyAsync(net->pinned, net->sums + 2 * net->partial_blocks, sizeof(double),
+                      cudaMemcpyDeviceToHost, net->stream));
+  MCU(cudaStreamSynchronize(net->stream));
+  if (loss) *loss = *reinterpret_cast<double*>(net->pinned);
+  return OFU_OK;
+}
+
+ofu_status ofu_mlp_train_step(ofu_mlp* net, const float* X, const float* t, const float* w,
+                              const int32_t* rows, int64_t B, float lr, double* loss) {
+  ST(mlp_ready(net));
+  if (!(lr > 0.0f)) {
+    net->err = "train_step: lr must be > 0";
+    return OFU_EINVAL;
+  }
+  ST(mlp_grad(net, X, t, w, rows, B));
+  net->step += 1;
+  MCU(launch_adam(net->params, net->m, net->v, net->grad, lr, net->step, net->stream));
+  if (loss) {
+    MCU(cudaMemcpyAsync(net->pinned, net->sums + 2 * net->partial_blocks, sizeof(double),
+                        cudaMemcpyDeviceToHost, net->stream));
+    MCU(cudaStreamSynchronize(net->stream));
+    *loss = *reinterpret_cast<double*>(net->pinned);
+  }
+  return OFU_OK;
+}
+
+ofu_status ofu_features(ofu_ctx* ctx, float* X, int64_t cap_rows) {
+  ST(check_built(ctx));
+  if (!X || cap_rows < ctx->n)
+    return fail(ctx, OFU_ECAPACITY, "features: X must hold N x 39 floats on the device");
+  Leaves& L = ctx->L[ctx->cur];
+  CU(launch_features(view_of(ctx), L.u, L.soff, ctx->samp[ctx->cur], ctx->prm.sample_fp16 != 0, X,
+                     ctx->stream));
+  return OFU_OK;
+}
+
+ofu_status ofu_warm_start(ofu_ctx* ctx, const ofu_mlp* net) {
+  ST(check_built(ctx));
+  if (!net) return fail(ctx, OFU_EINVAL, "warm_start: network is NULL");
+  CU(cudaStreamSynchronize(net->stream));   // the network's last update is complete
+  Leaves& L = ctx->L[ctx->cur];
+  CU(launch_warm_start(view_of(ctx), L.u, L.soff, ctx->samp[ctx->cur], ctx->prm.sample_fp16 != 0,
+                       net->params, L.ubar, ctx->stream));
+  CU(cudaMemcpyAsync(L.u, L.ubar, size_t(ctx->n) * sizeof(float), cudaMemcpyDeviceToDevice,
+                     ctx->stream));
+  // dual start consistent with the new field: lambda n on its edges
+  CU(launch_dual_init(view_of(ctx), L.u, L.p, float(ctx->prm.lambda), kWarmEdge, ctx->heavy,
+                      ctx->n_heavy_dual, ctx->stream));
+  return OFU_OK;
+}
+
 int64_t ofu_kernel_launches(void) { return launches_so_far(); }
 
 ofu_status ofu_profile(ofu_ctx* ctx, int32_t enable) {

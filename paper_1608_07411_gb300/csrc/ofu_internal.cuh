@@ -25,6 +25,11 @@ constexpr int32_t kEmpty = -1;
 constexpr uint32_t kIdxMask = (1u << 27) - 1;
 constexpr int kMaxDepth = 15;
 constexpr int64_t kMaxLeaves = int64_t(1) << 27;
+// Warm-start network: 39 inputs, two hidden layers of 64, one output.
+constexpr int kMlpIn = 39;
+constexpr int kMlpHid = 64;
+constexpr int kMlpParams = kMlpHid * kMlpIn + kMlpHid + kMlpHid * kMlpHid + kMlpHid + kMlpHid + 1;
+
 // Face lists longer than this make a leaf "heavy": its iteration updates run
 // as one block per leaf instead of one thread.
 constexpr int kHeavy = 16;
@@ -145,6 +150,23 @@ struct View {
 };
 
 }  // namespace ofu
+
+// ---------------------------------------------------------------------------
+// The warm-start network object (opaque to callers).
+struct ofu_mlp {
+  cudaStream_t stream = nullptr;
+  std::string err;
+  bool poisoned = false;
+  float* params = nullptr;   // kMlpParams
+  float* m = nullptr;        // Adam first moments
+  float* v = nullptr;        // Adam second moments
+  float* grad = nullptr;
+  float* partial = nullptr;  // per-block gradients
+  int64_t partial_blocks = 0;
+  double* sums = nullptr;    // per-block loss sums, then [loss, sum w]
+  int64_t step = 0;
+  void* pinned = nullptr;
+};
 
 // ---------------------------------------------------------------------------
 // The context (opaque to callers).
@@ -275,6 +297,9 @@ cudaError_t launch_copy_kept_samples(const int32_t* src, int64_t n, const uint32
 // Solver kernels.
 cudaError_t launch_dual(View v, const float* ubar, float* p, const float* sigma, float lambda,
                         const uint32_t* heavy, int n_heavy, cudaStream_t s);
+// p = lambda g / |g| where |g| >= g0 (g the gradient of u), else 0.
+cudaError_t launch_dual_init(View v, const float* u, float* p, float lambda, float g0,
+                             const uint32_t* heavy, int n_heavy, cudaStream_t s);
 cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const float* tau,
                           const uint32_t* soff, const void* samp, bool fp16, float gamma,
                           const uint32_t* heavy, int n_heavy, cudaStream_t s);
@@ -290,6 +315,21 @@ cudaError_t launch_energy_static(View v, const float* u, const float* p, const u
                                  const void* samp, bool fp16, double lambda, double gamma,
                                  double* scratch, cudaStream_t s);
 int energy_static_result_offset();
+
+// Warm-start network (mlp.cu).
+size_t mlp_tile_smem();
+int64_t mlp_grad_blocks(int64_t B);
+cudaError_t launch_features(View v, const float* u, const uint32_t* soff, const void* samp,
+                            bool fp16, float* X, cudaStream_t s);
+cudaError_t launch_mlp_forward(const float* params, const float* X, int64_t B, float* y,
+                               cudaStream_t s);
+cudaError_t launch_warm_start(View v, const float* u, const uint32_t* soff, const void* samp,
+                              bool fp16, const float* params, float* out, cudaStream_t s);
+cudaError_t launch_mlp_grad(const float* params, const float* X, const float* t, const float* w,
+                            const int32_t* rows, int64_t B, float* partial, double* psums,
+                            float* grad, double* loss2, cudaStream_t s);
+cudaError_t launch_adam(float* params, float* m, float* v, const float* g, float lr, int64_t step,
+                        cudaStream_t s);
 
 // Export helpers.
 cudaError_t launch_widen_samples(const void* samp, bool fp16, int64_t n, float* out,

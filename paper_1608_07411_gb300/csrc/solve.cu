@@ -70,11 +70,26 @@ __device__ __forceinline__ void dual_write(float* __restrict__ p, int64_t stride
   p[2 * stride + l] = q2;
 }
 
+// p of a piecewise-ramp field: lambda g / |g| where |g| >= g0, else 0 (the
+// optimal dual wherever the TV term is differentiable and the field has an
+// edge); used to start the dual together with a warm-started u.
+__device__ __forceinline__ void dual_init_write(float* __restrict__ p, int64_t stride, int64_t l,
+                                                const float g[3], float lambda, float g0) {
+  const float nrm = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+  const float sc = nrm >= g0 && nrm > 0.0f ? lambda / nrm : 0.0f;
+  p[l] = sc * g[0];
+  p[stride + l] = sc * g[1];
+  p[2 * stride + l] = sc * g[2];
+}
+
+// INIT = false: the dual step p <- proj(p + sigma grad ubar).
+// INIT = true:  p <- dual_init_write(grad ubar) with threshold g0 (sigma unused).
+template <bool INIT>
 __global__ void __launch_bounds__(kThreads) k_dual(View v, const float* __restrict__ ubar,
                                                    float* __restrict__ p,
                                                    const float* __restrict__ sigma, float lambda,
                                                    const uint32_t* __restrict__ heavy,
-                                                   int n_heavy_blocks) {
+                                                   int n_heavy_blocks, float g0) {
   if (int(blockIdx.x) < n_heavy_blocks) {
     // one heavy leaf per block; every thread takes part in the reductions
     __shared__ float red[kHeavyThreads / 32];
@@ -100,7 +115,12 @@ __global__ void __launch_bounds__(kThreads) k_dual(View v, const float* __restri
       }
       g[d] = block_sum(acc, red);
     }
-    if (threadIdx.x == 0) dual_write(p, v.stride, l, sigma[l], g, lambda);
+    if (threadIdx.x == 0) {
+      if (INIT)
+        dual_init_write(p, v.stride, l, g, lambda, g0);
+      else
+        dual_write(p, v.stride, l, sigma[l], g, lambda);
+    }
     return;
   }
   const int64_t l = int64_t(blockIdx.x - n_heavy_blocks) * blockDim.x + threadIdx.x;
@@ -129,7 +149,10 @@ __global__ void __launch_bounds__(kThreads) k_dual(View v, const float* __restri
     }
     g[d] = acc;
   }
-  dual_write(p, v.stride, l, sigma[l], g, lambda);
+  if (INIT)
+    dual_init_write(p, v.stride, l, g, lambda, g0);
+  else
+    dual_write(p, v.stride, l, sigma[l], g, lambda);
 }
 
 // Divergence of p at leaf l (gathers only).  Returns false, without a
@@ -442,8 +465,17 @@ inline unsigned blocks_for(int64_t n, int threads) { return unsigned((n + thread
 cudaError_t launch_dual(View v, const float* ubar, float* p, const float* sigma, float lambda,
                         const uint32_t* heavy, int n_heavy, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
-  k_dual<<<blocks_for(v.n, kThreads) + n_heavy, kThreads, 0, s>>>(v, ubar, p, sigma, lambda, heavy,
-                                                                   n_heavy);
+  k_dual<false><<<blocks_for(v.n, kThreads) + n_heavy, kThreads, 0, s>>>(v, ubar, p, sigma, lambda,
+                                                                          heavy, n_heavy, 0.0f);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dual_init(View v, const float* u, float* p, float lambda, float g0,
+                             const uint32_t* heavy, int n_heavy, cudaStream_t s) {
+  if (v.n <= 0) return cudaSuccess;
+  k_dual<true><<<blocks_for(v.n, kThreads) + n_heavy, kThreads, 0, s>>>(v, u, p, nullptr, lambda,
+                                                                         heavy, n_heavy, g0);
   count_launches(1);
   return cudaGetLastError();
 }

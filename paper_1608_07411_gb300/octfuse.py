@@ -69,6 +69,17 @@ _SIGS = {
     "ofu_export_neighbours": (_i32, [_vp, _i32, _vp, _vp, _i64, _P64]),
     "ofu_import_leaves": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp]),
     "ofu_set_state": (_i32, [_vp, _vp, _vp, _vp, _i64]),
+    "ofu_mlp_num_params": (_i64, []),
+    "ofu_mlp_create": (_i32, [_vp, ctypes.POINTER(_vp)]),
+    "ofu_mlp_destroy": (None, [_vp]),
+    "ofu_mlp_last_error": (ctypes.c_char_p, [_vp]),
+    "ofu_mlp_set_params": (_i32, [_vp, _vp]),
+    "ofu_mlp_get_params": (_i32, [_vp, _vp]),
+    "ofu_mlp_forward": (_i32, [_vp, _vp, _i64, _vp]),
+    "ofu_mlp_gradient": (_i32, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _PD]),
+    "ofu_mlp_train_step": (_i32, [_vp, _vp, _vp, _vp, _vp, _i64, ctypes.c_float, _PD]),
+    "ofu_features": (_i32, [_vp, _vp, _i64]),
+    "ofu_warm_start": (_i32, [_vp, _vp]),
     "ofu_energy_static": (_i32, [_vp, _vp]),
     "ofu_kernel_launches": (_i64, []),
     "ofu_profile": (_i32, [_vp, _i32]),
@@ -203,6 +214,65 @@ def ofu_import_leaves(ctx, keys, levels, n, u=None, p=None) -> None:
 
 def ofu_set_state(ctx, u, ubar, p, n) -> None:
     _check(ctx, load().ofu_set_state(ctx, _ptr(u), _ptr(ubar), _ptr(p), n))
+
+
+def _check_net(net, st):
+    if st != OFU_OK:
+        msg = load().ofu_mlp_last_error(net)
+        raise OfuError(st, msg.decode() if msg else "")
+
+
+def ofu_mlp_num_params() -> int:
+    return int(load().ofu_mlp_num_params())
+
+
+def ofu_mlp_create(stream: int = 0) -> int:
+    out = _vp()
+    _check_net(None, load().ofu_mlp_create(_vp(stream or None), ctypes.byref(out)))
+    return out.value
+
+
+def ofu_mlp_destroy(net) -> None:
+    load().ofu_mlp_destroy(net)
+
+
+def ofu_mlp_last_error(net=0) -> str:
+    msg = load().ofu_mlp_last_error(net or None)
+    return msg.decode() if msg else ""
+
+
+def ofu_mlp_set_params(net, params) -> None:
+    _check_net(net, load().ofu_mlp_set_params(net, _ptr(params)))
+
+
+def ofu_mlp_get_params(net, params) -> None:
+    _check_net(net, load().ofu_mlp_get_params(net, _ptr(params)))
+
+
+def ofu_mlp_forward(net, X, B, y) -> None:
+    _check_net(net, load().ofu_mlp_forward(net, _ptr(X), B, _ptr(y)))
+
+
+def ofu_mlp_gradient(net, X, t, w, rows, B, grad):
+    loss = ctypes.c_double()
+    _check_net(net, load().ofu_mlp_gradient(net, _ptr(X), _ptr(t), _ptr(w), _ptr(rows), B,
+                                            _ptr(grad), ctypes.byref(loss)))
+    return loss.value
+
+
+def ofu_mlp_train_step(net, X, t, w, rows, B, lr, want_loss=True):
+    loss = ctypes.c_double()
+    _check_net(net, load().ofu_mlp_train_step(net, _ptr(X), _ptr(t), _ptr(w), _ptr(rows), B, lr,
+                                              ctypes.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def ofu_features(ctx, X, cap_rows) -> None:
+    _check(ctx, load().ofu_features(ctx, _ptr(X), cap_rows))
+
+
+def ofu_warm_start(ctx, net) -> None:
+    _check(ctx, load().ofu_warm_start(ctx, net))
 
 
 def ofu_energy_static(ctx, out3=None):
