@@ -172,24 +172,47 @@ ofu_status rebuild_map(ofu_ctx* ctx) {
   return OFU_OK;
 }
 
-// Voxel map, face neighbours and step sizes of the current structure.
-ofu_status rebuild_topology(ofu_ctx* ctx) {
+// Voxel map, face neighbours, heavy leaves and step sizes of the current
+// structure.  One host synchronisation (the size of the neighbour lists, the
+// heavy-leaf counts and, when `samples_total` is given, the sample count).
+ofu_status rebuild_topology(ofu_ctx* ctx, const uint32_t* samples_total = nullptr) {
   const int64_t n = ctx->n;
   ST(rebuild_map(ctx));
   uint32_t* ovfc;
   uint32_t* tmp;
-  ST(ensure(ctx, B_OVFC, size_t(6 * n + 1), &ovfc));
-  ST(ensure(ctx, B_SCAN, scan_tmp_items<uint32_t>(6 * n) * 2, &tmp));
   uint32_t* longq;
   uint64_t* small;
+  ST(ensure(ctx, B_OVFC, size_t(6 * n + 1), &ovfc));
+  ST(ensure(ctx, B_SCAN, scan_tmp_items<uint32_t>(6 * n) * 2, &tmp));
   ST(ensure(ctx, B_LONGQ, size_t(6 * n), &longq));
-  ST(ensure(ctx, B_SMALL, 8, &small));
+  ST(ensure(ctx, B_SMALL, 16, &small));
+  if (ctx->heavy_cap < n) {
+    if (ctx->heavy) CU(cudaFree(ctx->heavy));
+    ctx->heavy = nullptr;
+    ctx->heavy_cap = 0;
+    const int64_t cap = std::max<int64_t>(n + n / 4, 1024);
+    CU(cudaMalloc(&ctx->heavy, 2 * size_t(cap) * sizeof(uint32_t)));
+    ctx->heavy_cap = cap;
+  }
   unsigned long long* nlong = reinterpret_cast<unsigned long long*>(small + 8);
+  unsigned long long* hcount = reinterpret_cast<unsigned long long*>(small + 9);
+  Leaves& L = ctx->L[ctx->cur];
   View v = view_of(ctx);
-  CU(launch_nbr_count(v, ovfc, longq, nlong, ctx->stream));
+  CU(launch_nbr_count(v, L.nbr, ovfc, longq, nlong, ctx->stream));
+  CU(launch_heavy(v, ovfc, ctx->heavy, ctx->heavy + ctx->heavy_cap, hcount, ctx->stream));
   CU(scan_exclusive<uint32_t>(ovfc, ovfc, 6 * n, tmp, ctx->stream));
-  uint32_t total = 0;
-  ST(read_back(ctx, ovfc + 6 * n, sizeof(uint32_t), &total));
+  // one read-back: [list total (u32), samples (u32)] in slot 11, heavy counts in 9, 10
+  CU(cudaMemcpyAsync(reinterpret_cast<uint32_t*>(small + 11), ovfc + 6 * n, sizeof(uint32_t),
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  if (samples_total)
+    CU(cudaMemcpyAsync(reinterpret_cast<uint32_t*>(small + 11) + 1, samples_total, sizeof(uint32_t),
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  uint64_t hs[3];
+  ST(read_back(ctx, small + 9, 3 * sizeof(uint64_t), hs));
+  ctx->n_heavy_dual = int(hs[0]);
+  ctx->n_heavy_primal = int(hs[1]);
+  const uint32_t total = uint32_t(hs[2] & 0xffffffffu);
+  if (samples_total) ctx->n_samples = int64_t(hs[2] >> 32);
   if (int64_t(total) + 1 > ctx->ovf_cap) {
     if (ctx->ovf) CU(cudaFree(ctx->ovf));
     ctx->ovf = nullptr;
@@ -199,24 +222,8 @@ ofu_status rebuild_topology(ofu_ctx* ctx) {
     ctx->ovf_cap = cap;
   }
   v = view_of(ctx);
-  Leaves& L = ctx->L[ctx->cur];
   CU(launch_nbr_fill(v, ovfc, L.nbr, ctx->ovf, longq, nlong, ctx->stream));
   v = view_of(ctx);
-  // heavy leaves (long face lists) for the step sizes and iteration kernels
-  if (ctx->heavy_cap < n) {
-    if (ctx->heavy) CU(cudaFree(ctx->heavy));
-    ctx->heavy = nullptr;
-    ctx->heavy_cap = 0;
-    const int64_t cap = std::max<int64_t>(n + n / 4, 1024);
-    CU(cudaMalloc(&ctx->heavy, 2 * size_t(cap) * sizeof(uint32_t)));
-    ctx->heavy_cap = cap;
-  }
-  CU(launch_heavy(v, ctx->heavy, ctx->heavy + ctx->heavy_cap,
-                  reinterpret_cast<unsigned long long*>(small + 6), ctx->stream));
-  uint64_t hc[2];
-  ST(read_back(ctx, small + 6, 2 * sizeof(uint64_t), hc));
-  ctx->n_heavy_dual = int(hc[0]);
-  ctx->n_heavy_primal = int(hc[1]);
   CU(launch_precond(v, L.tau, L.sigma, ctx->heavy + ctx->heavy_cap, ctx->n_heavy_primal,
                     ctx->stream));
   return OFU_OK;
@@ -229,15 +236,15 @@ ofu_status integrate_all(ofu_ctx* ctx, bool init) {
   const Geo g = geo_of(ctx);
   uint32_t* tmp;
   ST(ensure(ctx, B_SCAN, scan_tmp_items<uint32_t>(n) * 2, &tmp));
-  CU(launch_leaf_count(L.key, L.level, nullptr, n, ctx->depth, ctx->cams, ctx->F, ctx->H, ctx->W,
-                       g, L.soff, ctx->stream));
+  CU(launch_leaf_count(L.key, L.level, nullptr, nullptr, n, ctx->depth, ctx->cams, ctx->F, ctx->H,
+                       ctx->W, g, L.soff, ctx->stream));
   CU(scan_exclusive<uint32_t>(L.soff, L.soff, n, tmp, ctx->stream));
   uint32_t total = 0;
   ST(read_back(ctx, L.soff + n, sizeof(uint32_t), &total));
   ST(ensure_samples(ctx, ctx->cur, int64_t(total)));
   ctx->n_samples = total;
-  CU(launch_leaf_fill(L.key, L.level, nullptr, n, ctx->depth, ctx->cams, ctx->F, ctx->H, ctx->W,
-                      g, L.soff, ctx->samp[ctx->cur], ctx->prm.sample_fp16 != 0,
+  CU(launch_leaf_fill(L.key, L.level, nullptr, nullptr, n, ctx->depth, ctx->cams, ctx->F, ctx->H,
+                      ctx->W, g, L.soff, ctx->samp[ctx->cur], ctx->prm.sample_fp16 != 0,
                       init ? L.u : nullptr, init ? L.ubar : nullptr, ctx->stream));
   if (init) CU(cudaMemsetAsync(L.p, 0, 3 * L.cap * sizeof(float), ctx->stream));
   return OFU_OK;
@@ -391,6 +398,7 @@ ofu_status ofu_integrate_frames(ofu_ctx* ctx, int32_t F, int32_t H, int32_t W, c
   CU(cudaMalloc(&ctx->cams, size_t(F) * sizeof(Cam)));
   CU(cudaMemcpyAsync(ctx->depth, depth, dbytes, cudaMemcpyDefault, ctx->stream));
   CU(cudaMemcpyAsync(ctx->cams, cams.data(), size_t(F) * sizeof(Cam), cudaMemcpyHostToDevice, ctx->stream));
+  CU(launch_range_map(ctx->depth, ctx->cams, F, H, W, ctx->stream));
   ctx->F = F;
   ctx->H = H;
   ctx->W = W;
@@ -506,28 +514,27 @@ ofu_status ofu_restructure(ofu_ctx* ctx, int64_t* n_split, int64_t* n_join, int6
   ST(ensure(ctx, B_BIG, size_t(n), &big));
   CU(launch_emit(v, L.u, L.p, outc, jl, N2.key, N2.level, N2.u, N2.ubar, N2.p, N2.cap, src, big,
                  reinterpret_cast<unsigned long long*>(small + 4), ctx->stream));
-  CU(cudaMemsetAsync(small + 3, 0, sizeof(uint64_t), ctx->stream));
-  CU(launch_new_list(src, n_new, list, reinterpret_cast<unsigned long long*>(small + 3), ctx->stream));
+  // new leaves (split children, joined nodes) are listed on the device and
+  // integrated without a host round trip; the sample buffer is sized for the
+  // worst case (every frame observes every new leaf)
+  unsigned long long* nlist = reinterpret_cast<unsigned long long*>(small + 3);
+  CU(cudaMemsetAsync(nlist, 0, sizeof(uint64_t), ctx->stream));
+  CU(launch_new_list(src, n_new, list, nlist, ctx->stream));
   CU(launch_kept_counts(src, L.soff, n_new, N2.soff, ctx->stream));
-  uint64_t hl = 0;
-  ST(read_back(ctx, small + 3, sizeof(uint64_t), &hl));
   const Geo g = geo_of(ctx);
-  CU(launch_leaf_count(N2.key, N2.level, list, int64_t(hl), ctx->depth, ctx->cams, ctx->F, ctx->H,
+  CU(launch_leaf_count(N2.key, N2.level, list, nlist, n_new, ctx->depth, ctx->cams, ctx->F, ctx->H,
                        ctx->W, g, N2.soff, ctx->stream));
   CU(scan_exclusive<uint32_t>(N2.soff, N2.soff, n_new, tmp32, ctx->stream));
-  uint32_t total = 0;
-  ST(read_back(ctx, N2.soff + n_new, sizeof(uint32_t), &total));
-  ST(ensure_samples(ctx, nx, int64_t(total)));
+  ST(ensure_samples(ctx, nx, n_new * int64_t(ctx->F)));
   const bool h16 = ctx->prm.sample_fp16 != 0;
   CU(launch_copy_kept_samples(src, n_new, L.soff, ctx->samp[ctx->cur], N2.soff, ctx->samp[nx], h16,
                               ctx->stream));
-  CU(launch_leaf_fill(N2.key, N2.level, list, int64_t(hl), ctx->depth, ctx->cams, ctx->F, ctx->H,
+  CU(launch_leaf_fill(N2.key, N2.level, list, nlist, n_new, ctx->depth, ctx->cams, ctx->F, ctx->H,
                       ctx->W, g, N2.soff, ctx->samp[nx], h16, nullptr, nullptr, ctx->stream));
   ctx->cur = nx;
   ctx->n = n_new;
-  ctx->n_samples = total;
   (void)D;
-  ST(rebuild_topology(ctx));
+  ST(rebuild_topology(ctx, N2.soff + n_new));
   if (n_split) *n_split = ns;
   if (n_join) *n_join = nj;
   if (n_leaves) *n_leaves = n_new;
@@ -541,7 +548,8 @@ ofu_status ofu_energy(ofu_ctx* ctx, double* primal, double* dual, double* gap) {
   ST(ensure(ctx, B_PART, energy_tmp_bytes(ctx->n) / sizeof(double) + 4, &part));
   small = part + energy_tmp_bytes(ctx->n) / sizeof(double);
   CU(launch_energy(view_of(ctx), L.u, L.p, L.soff, ctx->samp[ctx->cur], ctx->prm.sample_fp16 != 0,
-                   ctx->prm.lambda, ctx->prm.gamma, part, small, ctx->stream));
+                   ctx->prm.lambda, ctx->prm.gamma, ctx->heavy + ctx->heavy_cap, ctx->n_heavy_primal,
+                   part, small, ctx->stream));
   double h[3];
   ST(read_back(ctx, small, 3 * sizeof(double), h));
   if (primal) *primal = h[0];
@@ -750,8 +758,8 @@ ofu_status ofu_energy_static(ofu_ctx* ctx, double* out3) {
   CU(energy_static_scratch(&scratch));
   Leaves& L = ctx->L[ctx->cur];
   CU(launch_energy_static(view_of(ctx), L.u, L.p, L.soff, ctx->samp[ctx->cur],
-                          ctx->prm.sample_fp16 != 0, ctx->prm.lambda, ctx->prm.gamma, scratch,
-                          ctx->stream));
+                          ctx->prm.sample_fp16 != 0, ctx->prm.lambda, ctx->prm.gamma,
+                          ctx->heavy + ctx->heavy_cap, ctx->n_heavy_primal, scratch, ctx->stream));
   CU(cudaMemcpyAsync(out3, scratch + energy_static_result_offset(), 3 * sizeof(double),
                      cudaMemcpyDefault, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));

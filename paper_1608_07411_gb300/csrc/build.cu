@@ -231,6 +231,17 @@ __global__ void __launch_bounds__(256) k_dense_u0(const float* __restrict__ dept
   }
 }
 
+__global__ void k_range_map(float* __restrict__ depth, const Cam* __restrict__ cams, int F, int H,
+                            int W) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t per = int64_t(H) * W;
+  if (i >= per * F) return;
+  const int f = int(i / per);
+  const int64_t r = i - int64_t(f) * per;
+  const int py = int(r / W), px = int(r - int64_t(py) * W);
+  depth[i] = pixel_range(cams[f], depth[i], px, py);
+}
+
 // ---------------------------------------------------------------------------
 // Eq. 2 pyramid: per node the min and max of u0 over its finest voxels.
 // Level L occupies [(8^L - 1)/7, (8^(L+1) - 1)/7) of mn / mx.
@@ -313,13 +324,16 @@ __device__ __forceinline__ void leaf_centre(uint64_t key, int level, const Geo& 
 
 __global__ void __launch_bounds__(256) k_leaf_count(const uint64_t* __restrict__ key,
                                                     const uint8_t* __restrict__ level,
-                                                    const uint32_t* __restrict__ list, int64_t n,
+                                                    const uint32_t* __restrict__ list,
+                                                    const unsigned long long* __restrict__ nlist,
+                                                    int64_t n,
                                                     const float* __restrict__ depth,
                                                     const Cam* __restrict__ cams, int F, int H,
                                                     int W, Geo g, uint32_t* __restrict__ count) {
   extern __shared__ float4 smem_dyn[];
   Cam* sc = reinterpret_cast<Cam*>(smem_dyn);
   stage_cams(sc, cams, F);
+  if (nlist) n = int64_t(*nlist);
   const int warp = threadIdx.x >> 5, lane = lane_id();
   for (int64_t j = int64_t(blockIdx.x) * kWarpsPerBlock + warp; j < n;
        j += int64_t(gridDim.x) * kWarpsPerBlock) {
@@ -339,13 +353,15 @@ __global__ void __launch_bounds__(256) k_leaf_count(const uint64_t* __restrict__
 template <int P, typename T>
 __global__ void __launch_bounds__(256) k_leaf_fill(
     const uint64_t* __restrict__ key, const uint8_t* __restrict__ level,
-    const uint32_t* __restrict__ list, int64_t n, const float* __restrict__ depth,
+    const uint32_t* __restrict__ list, const unsigned long long* __restrict__ nlist, int64_t n,
+    const float* __restrict__ depth,
     const Cam* __restrict__ cams, int F, int H, int W, Geo g, const uint32_t* __restrict__ soff,
     T* __restrict__ samp, float* __restrict__ u, float* __restrict__ ubar) {
   extern __shared__ float4 smem_dyn[];
   Cam* sc = reinterpret_cast<Cam*>(smem_dyn);
   float* bufs = reinterpret_cast<float*>(sc + F);
   stage_cams(sc, cams, F);
+  if (nlist) n = int64_t(*nlist);
   const int warp = threadIdx.x >> 5, lane = lane_id();
   float* a = bufs + warp * P;
   for (int64_t j = int64_t(blockIdx.x) * kWarpsPerBlock + warp; j < n;
@@ -492,7 +508,9 @@ __device__ __forceinline__ uint32_t even_bits(uint32_t x) {
   return x;
 }
 
-// Leaf listed at face voxel i (2-D Morton index), or -1.
+// Leaf listed at face voxel i (2-D Morton index), or -1.  For a square of
+// edge 2 the (subdivided) neighbour cube's children are finest voxels, so
+// every face voxel is its own leaf and no key check is needed.
 __device__ __forceinline__ int64_t face_rep(const View& v, const FaceSquare& q, uint32_t i) {
   const uint32_t a = q.c1 + even_bits(i), b = q.c2 + even_bits(i >> 1);
   uint32_t c[3];
@@ -500,6 +518,7 @@ __device__ __forceinline__ int64_t face_rep(const View& v, const FaceSquare& q, 
   c[q.t1] = a;
   c[q.t2] = b;
   const uint32_t m = v.map[morton(c[0], c[1], c[2])];
+  if (q.h == 2) return int64_t(m);
   const uint64_t km = v.key[m];
   return (compact3(km >> q.t1) == a && compact3(km >> q.t2) == b) ? int64_t(m) : -1;
 }
@@ -508,50 +527,61 @@ __device__ __forceinline__ int64_t face_rep(const View& v, const FaceSquare& q, 
 // larger ones by a block (k_nbr_long_*).
 constexpr uint32_t kThreadSquare = 16;
 
-__global__ void k_nbr_count(View v, uint32_t* __restrict__ ovf_count, uint32_t* __restrict__ longq,
-                            unsigned long long* __restrict__ nlong) {
-  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= 6 * v.n) return;
-  const int face = int(t / v.n);
-  const int64_t l = t - int64_t(face) * v.n;
-  const FaceHit f = face_query(v, l, face);
-  uint32_t c = 0;
-  if (f.kind == 2) {
-    const FaceSquare q = face_square(v, l, face);
-    if (q.h * q.h > kThreadSquare) {
-      longq[atomicAdd(nlong, 1ull)] = uint32_t(t);   // counted by k_nbr_long_count
-    } else {
-      c = 1;
-      for (uint32_t i = 0; i < q.h * q.h; ++i) c += face_rep(v, q, i) >= 0;
-    }
-  }
-  ovf_count[t] = c;
-}
+// Entry of a face whose finer-neighbour list is not yet written.
+constexpr int32_t kListPending = int32_t(0x80000000u | 0x7ffffffeu);
 
-__global__ void k_nbr_fill(View v, const uint32_t* __restrict__ ovf_off, int32_t* __restrict__ nbr,
-                           int32_t* __restrict__ ovf) {
+// One thread per (leaf, face).  Single neighbours and boundaries are final
+// here; finer lists are counted (small squares by this thread, larger ones
+// queued for a block) and marked pending for the fill pass.
+__global__ void k_nbr_count(View v, int32_t* __restrict__ nbr, uint32_t* __restrict__ ovf_count,
+                            uint32_t* __restrict__ longq, unsigned long long* __restrict__ nlong) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= 6 * v.n) return;
   const int face = int(t / v.n);
   const int64_t l = t - int64_t(face) * v.n;
   const FaceHit f = face_query(v, l, face);
   int32_t e = kEmpty;
+  uint32_t cnt = 0;
   if (f.kind == 1) {
     e = make_single(f.m, f.mlev);
   } else if (f.kind == 2) {
-    const uint32_t st = ovf_off[t];
-    e = make_list(st);
+    e = kListPending;
     const FaceSquare q = face_square(v, l, face);
-    if (q.h * q.h <= kThreadSquare) {
-      uint32_t c = 0;
-      for (uint32_t i = 0; i < q.h * q.h; ++i) {
-        const int64_t m = face_rep(v, q, i);
-        if (m >= 0) ovf[st + 1 + c++] = make_single(uint32_t(m), v.level[m]);
-      }
-      ovf[st] = int32_t(c);
+    cnt = 1;
+    if (q.h * q.h > kThreadSquare) {
+      longq[atomicAdd(nlong, 1ull)] = uint32_t(t);   // k_nbr_long_count adds the leaves
+    } else {
+#pragma unroll 4
+      for (uint32_t i = 0; i < q.h * q.h; ++i) cnt += face_rep(v, q, i) >= 0;
     }
   }
   nbr[int64_t(face) * v.stride + l] = e;
+  ovf_count[t] = cnt;
+}
+
+// Writes the finer-neighbour lists of small squares (pending entries only;
+// every other thread returns after one load) and points each pending entry
+// at its list.
+__global__ void k_nbr_fill(View v, const uint32_t* __restrict__ ovf_off, int32_t* __restrict__ nbr,
+                           int32_t* __restrict__ ovf) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= 6 * v.n) return;
+  const int face = int(t / v.n);
+  const int64_t l = t - int64_t(face) * v.n;
+  const int64_t slot = int64_t(face) * v.stride + l;
+  if (nbr[slot] != kListPending) return;
+  const uint32_t st = ovf_off[t];
+  const FaceSquare q = face_square(v, l, face);
+  if (q.h * q.h <= kThreadSquare) {
+    uint32_t c = 0;
+#pragma unroll 4
+    for (uint32_t i = 0; i < q.h * q.h; ++i) {
+      const int64_t m = face_rep(v, q, i);
+      if (m >= 0) ovf[st + 1 + c++] = make_single(uint32_t(m), v.level[m]);
+    }
+    ovf[st] = int32_t(c);
+  }
+  nbr[slot] = make_list(st);
 }
 
 // Block-wide ordered walk of a face square: calls emit(position, leaf) for
@@ -725,14 +755,16 @@ __global__ void k_precond(View v, float* __restrict__ tau, float* __restrict__ s
   tau[l] = col > 0.0f ? 1.0f / col : 1.0f;
 }
 
-__global__ void k_heavy(View v, uint32_t* __restrict__ hd, uint32_t* __restrict__ hp,
-                        unsigned long long* __restrict__ counts) {
+// Heavy leaves from the list counts of the neighbour pass (1 + list length
+// per list face, 0 otherwise), before those counts are scanned.
+__global__ void k_heavy(View v, const uint32_t* __restrict__ ovf_count, uint32_t* __restrict__ hd,
+                        uint32_t* __restrict__ hp, unsigned long long* __restrict__ counts) {
   const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (l >= v.n) return;
   bool dual = false, primal = false;
   for (int face = 0; face < 6; ++face) {
-    const int32_t e = v.nbr[int64_t(face) * v.stride + l];
-    if (is_list(e) && v.ovf[list_start(e)] > kHeavy) {
+    const uint32_t c = ovf_count[int64_t(face) * v.n + l];
+    if (c > uint32_t(kHeavy) + 1) {
       primal = true;
       if (face < 3) dual = true;
     }
@@ -1091,6 +1123,13 @@ cudaError_t launch_dense_u0(const float* depth, const Cam* cams, int F, int H, i
   }
 }
 
+cudaError_t launch_range_map(float* depth, const Cam* cams, int F, int H, int W, cudaStream_t s) {
+  const int64_t n = int64_t(F) * H * W;
+  k_range_map<<<blocks_for(n, 256), 256, 0, s>>>(depth, cams, F, H, W);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pyramid(const double* u0, int D, double* mn, double* mx, cudaStream_t s) {
   // level D-1 from the voxels, then upwards
   int64_t nn = int64_t(1) << (3 * (D - 1));
@@ -1124,60 +1163,61 @@ cudaError_t launch_emit_constructed(const uint32_t* flags, const uint32_t* pos, 
 }
 
 cudaError_t launch_leaf_count(const uint64_t* key, const uint8_t* level, const uint32_t* list,
-                              int64_t n, const float* depth, const Cam* cams, int F, int H, int W,
-                              Geo g, uint32_t* count, cudaStream_t s) {
+                              const unsigned long long* nlist, int64_t n, const float* depth,
+                              const Cam* cams, int F, int H, int W, Geo g, uint32_t* count,
+                              cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const size_t sm = size_t(F) * sizeof(Cam);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_leaf_count, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-  k_leaf_count<<<warp_grid(n), 32 * kWarpsPerBlock, sm, s>>>(key, level, list, n, depth, cams, F,
-                                                              H, W, g, count);
+  k_leaf_count<<<warp_grid(n), 32 * kWarpsPerBlock, sm, s>>>(key, level, list, nlist, n, depth,
+                                                              cams, F, H, W, g, count);
   count_launches(1);
   return cudaGetLastError();
 }
 
 template <int P, typename T>
 static cudaError_t leaf_fill_p(const uint64_t* key, const uint8_t* level, const uint32_t* list,
-                               int64_t n, const float* depth, const Cam* cams, int F, int H, int W,
-                               Geo g, const uint32_t* soff, void* samp, float* u, float* ubar,
-                               cudaStream_t s) {
+                               const unsigned long long* nlist, int64_t n, const float* depth,
+                               const Cam* cams, int F, int H, int W, Geo g, const uint32_t* soff,
+                               void* samp, float* u, float* ubar, cudaStream_t s) {
   const size_t sm = size_t(F) * sizeof(Cam) + size_t(kWarpsPerBlock) * P * sizeof(float);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_leaf_fill<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
   k_leaf_fill<P, T><<<warp_grid(n), 32 * kWarpsPerBlock, sm, s>>>(
-      key, level, list, n, depth, cams, F, H, W, g, soff, reinterpret_cast<T*>(samp), u, ubar);
+      key, level, list, nlist, n, depth, cams, F, H, W, g, soff, reinterpret_cast<T*>(samp), u, ubar);
   count_launches(1);
   return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t leaf_fill_t(const uint64_t* key, const uint8_t* level, const uint32_t* list,
-                               int64_t n, const float* depth, const Cam* cams, int F, int H, int W,
-                               Geo g, const uint32_t* soff, void* samp, float* u, float* ubar,
-                               cudaStream_t s) {
+                               const unsigned long long* nlist, int64_t n, const float* depth,
+                               const Cam* cams, int F, int H, int W, Geo g, const uint32_t* soff,
+                               void* samp, float* u, float* ubar, cudaStream_t s) {
   switch (pad_frames(F)) {
-    case 32: return leaf_fill_p<32, T>(key, level, list, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
-    case 64: return leaf_fill_p<64, T>(key, level, list, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
-    case 128: return leaf_fill_p<128, T>(key, level, list, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
-    case 256: return leaf_fill_p<256, T>(key, level, list, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
-    case 512: return leaf_fill_p<512, T>(key, level, list, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
+    case 32: return leaf_fill_p<32, T>(key, level, list, nlist, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
+    case 64: return leaf_fill_p<64, T>(key, level, list, nlist, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
+    case 128: return leaf_fill_p<128, T>(key, level, list, nlist, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
+    case 256: return leaf_fill_p<256, T>(key, level, list, nlist, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
+    case 512: return leaf_fill_p<512, T>(key, level, list, nlist, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_leaf_fill(const uint64_t* key, const uint8_t* level, const uint32_t* list,
-                             int64_t n, const float* depth, const Cam* cams, int F, int H, int W,
-                             Geo g, const uint32_t* soff, void* samp, bool fp16, float* u,
-                             float* ubar, cudaStream_t s) {
+                             const unsigned long long* nlist, int64_t n, const float* depth,
+                             const Cam* cams, int F, int H, int W, Geo g, const uint32_t* soff,
+                             void* samp, bool fp16, float* u, float* ubar, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  return fp16 ? leaf_fill_t<__half>(key, level, list, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s)
-              : leaf_fill_t<float>(key, level, list, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
+  return fp16 ? leaf_fill_t<__half>(key, level, list, nlist, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s)
+              : leaf_fill_t<float>(key, level, list, nlist, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
 }
 
-cudaError_t launch_nbr_count(View v, uint32_t* ovf_count, uint32_t* longq,
+cudaError_t launch_nbr_count(View v, int32_t* nbr, uint32_t* ovf_count, uint32_t* longq,
                              unsigned long long* nlong, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(nlong, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k_nbr_count<<<blocks_for(6 * v.n, 256), 256, 0, s>>>(v, ovf_count, longq, nlong);
+  k_nbr_count<<<blocks_for(6 * v.n, 256), 256, 0, s>>>(v, nbr, ovf_count, longq, nlong);
   count_launches(1);
   k_nbr_long_count<<<unsigned(sm_count() * 8), 256, 0, s>>>(v, longq, nlong, ovf_count);
   count_launches(1);
@@ -1203,11 +1243,11 @@ cudaError_t launch_precond(View v, float* tau, float* sigma, const uint32_t* hea
   return cudaGetLastError();
 }
 
-cudaError_t launch_heavy(View v, uint32_t* heavy_dual, uint32_t* heavy_primal,
-                         unsigned long long* counts, cudaStream_t s) {
+cudaError_t launch_heavy(View v, const uint32_t* ovf_count, uint32_t* heavy_dual,
+                         uint32_t* heavy_primal, unsigned long long* counts, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s);
   if (e != cudaSuccess || v.n <= 0) return e;
-  k_heavy<<<blocks_for(v.n, 256), 256, 0, s>>>(v, heavy_dual, heavy_primal, counts);
+  k_heavy<<<blocks_for(v.n, 256), 256, 0, s>>>(v, ovf_count, heavy_dual, heavy_primal, counts);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -85,10 +85,22 @@ struct Geo {
   int D;
 };
 
+// Range along the ray of pixel (px, py): D * |K^-1 (px + 0.5, py + 0.5, 1)|,
+// float32, one rounding per operation.  Depends on the pixel only, so it is
+// precomputed once per frame set (the "range map"); 0, negative or NaN depth
+// stays non-positive or NaN, +inf stays +inf.
+__device__ __forceinline__ float pixel_range(const Cam& k, float d, int px, int py) {
+  const float a = __fdiv_rn(__fsub_rn(__fadd_rn(float(px), 0.5f), k.cx), k.fx);
+  const float b = __fdiv_rn(__fsub_rn(__fadd_rn(float(py), 0.5f), k.cy), k.fy);
+  const float rl = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)), 1.0f));
+  return __fmul_rn(d, rl);
+}
+
 // Eq. 1 for one point and one frame, float32 with one rounding per
 // operation in a fixed order (no contraction into fused multiply-adds).
-// Returns false when the frame does not observe the point (w = 0).
-__device__ __forceinline__ bool eq1_sample(const Cam& k, const float* __restrict__ depth, int H,
+// `range` is the frame's range map.  Returns false when the frame does not
+// observe the point (w = 0).
+__device__ __forceinline__ bool eq1_sample(const Cam& k, const float* __restrict__ range, int H,
                                            int W, float x, float y, float z, float delta, float eta,
                                            float* f) {
   const float dx = __fsub_rn(x, k.c[0]);
@@ -103,12 +115,8 @@ __device__ __forceinline__ bool eq1_sample(const Cam& k, const float* __restrict
   if (!(u >= 0.0f && u < float(W) && v >= 0.0f && v < float(H))) return false;
   const int px = int(floorf(u));
   const int py = int(floorf(v));
-  const float d = __ldg(depth + size_t(py) * W + px);
-  if (!(d > 0.0f)) return false;
-  const float a = __fdiv_rn(__fsub_rn(__fadd_rn(float(px), 0.5f), k.cx), k.fx);
-  const float b = __fdiv_rn(__fsub_rn(__fadd_rn(float(py), 0.5f), k.cy), k.fy);
-  const float rl = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)), 1.0f));
-  const float rng = __fmul_rn(d, rl);
+  const float rng = __ldg(range + size_t(py) * W + px);
+  if (!(rng > 0.0f)) return false;   // depth 0, negative or NaN
   const float dist = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)));
   const float phi = __fsub_rn(rng, dist);
   if (!(phi >= -eta)) return false;
@@ -179,7 +187,7 @@ struct ofu_ctx {
 
   // frames (copied in by ofu_integrate_frames)
   int F = 0, H = 0, W = 0;
-  float* depth = nullptr;
+  float* depth = nullptr;      // range maps after ofu_integrate_frames (pixel_range)
   ofu::Cam* cams = nullptr;
   bool have_frames = false;
 
@@ -234,6 +242,9 @@ size_t scan_tmp_items(int64_t n);
 template <typename T>
 cudaError_t scan_exclusive(const T* in, T* out, int64_t n, T* tmp, cudaStream_t s);
 
+// Depth maps -> range maps in place (see pixel_range).
+cudaError_t launch_range_map(float* depth, const Cam* cams, int F, int H, int W, cudaStream_t s);
+
 // Median field at finest-voxel centres (Morton order), then the Eq. 2 min/max
 // pyramid and the per-voxel leaf flags.
 cudaError_t launch_dense_u0(const float* depth, const Cam* cams, int F, int H, int W, Geo g,
@@ -245,25 +256,29 @@ cudaError_t launch_emit_constructed(const uint32_t* flags, const uint32_t* pos,
                                     const double* mn, const double* mx, int D, double spread_tau,
                                     uint64_t* key, uint8_t* level, cudaStream_t s);
 
-// Eq. 1 samples of leaves: counts (W) and the sorted CSR fill.  `list` selects
-// leaves (nullptr = all n).  fill also writes u = ubar = median when init.
+// Eq. 1 samples of leaves: counts (W) and the sorted CSR fill.  `list`
+// selects leaves (nullptr = all n); with `nlist` (device) the number of listed
+// leaves is read on the device and n is only the grid's upper bound.  fill
+// also writes u = ubar = median when u is given.
 cudaError_t launch_leaf_count(const uint64_t* key, const uint8_t* level, const uint32_t* list,
-                              int64_t n, const float* depth, const Cam* cams, int F, int H, int W,
-                              Geo g, uint32_t* count, cudaStream_t s);
+                              const unsigned long long* nlist, int64_t n, const float* depth,
+                              const Cam* cams, int F, int H, int W, Geo g, uint32_t* count,
+                              cudaStream_t s);
 cudaError_t launch_leaf_fill(const uint64_t* key, const uint8_t* level, const uint32_t* list,
-                             int64_t n, const float* depth, const Cam* cams, int F, int H, int W,
-                             Geo g, const uint32_t* soff, void* samp, bool fp16, float* u,
-                             float* ubar, cudaStream_t s);
+                             const unsigned long long* nlist, int64_t n, const float* depth,
+                             const Cam* cams, int F, int H, int W, Geo g, const uint32_t* soff,
+                             void* samp, bool fp16, float* u, float* ubar, cudaStream_t s);
 
 // Heavy leaves: dual-heavy when a +face list exceeds kHeavy, primal-heavy
-// when any face list does (counts[0], counts[1] are atomically appended to).
-cudaError_t launch_heavy(View v, uint32_t* heavy_dual, uint32_t* heavy_primal,
-                         unsigned long long* counts, cudaStream_t s);
+// when any face list does, read from the unscanned neighbour-list counts
+// (counts[0], counts[1] are atomically appended to).
+cudaError_t launch_heavy(View v, const uint32_t* ovf_count, uint32_t* heavy_dual,
+                         uint32_t* heavy_primal, unsigned long long* counts, cudaStream_t s);
 
 // Face neighbours (two passes) and step sizes.
 // Face neighbours: count pass (long lists queued in longq and counted by a
 // block each), then the fill.
-cudaError_t launch_nbr_count(View v, uint32_t* ovf_count, uint32_t* longq,
+cudaError_t launch_nbr_count(View v, int32_t* nbr, uint32_t* ovf_count, uint32_t* longq,
                              unsigned long long* nlong, cudaStream_t s);
 cudaError_t launch_nbr_fill(View v, const uint32_t* ovf_off, int32_t* nbr, int32_t* ovf,
                             const uint32_t* longq, const unsigned long long* nlong,
@@ -306,14 +321,16 @@ cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const f
 size_t energy_tmp_bytes(int64_t n);
 cudaError_t launch_energy(View v, const float* u, const float* p, const uint32_t* soff,
                           const void* samp, bool fp16, double lambda, double gamma,
-                          double* partial, double* out3, cudaStream_t s);
+                          const uint32_t* heavy, int n_heavy, double* partial, double* out3,
+                          cudaStream_t s);
 
 // Energy with its scratch in a file-scope device array (solve.cu).
 int64_t energy_static_max_leaves();
 cudaError_t energy_static_scratch(double** ptr);
 cudaError_t launch_energy_static(View v, const float* u, const float* p, const uint32_t* soff,
                                  const void* samp, bool fp16, double lambda, double gamma,
-                                 double* scratch, cudaStream_t s);
+                                 const uint32_t* heavy, int n_heavy, double* scratch,
+                                 cudaStream_t s);
 int energy_static_result_offset();
 
 // Warm-start network (mlp.cu).

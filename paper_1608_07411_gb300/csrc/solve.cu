@@ -123,25 +123,26 @@ __global__ void __launch_bounds__(kThreads) k_dual(View v, const float* __restri
     }
     return;
   }
-  const int64_t l = int64_t(blockIdx.x - n_heavy_blocks) * blockDim.x + threadIdx.x;
-  if (l >= v.n) return;
+  // light path: one leaf per thread, 32-bit indices (N < 2^27), rows hoisted
+  const uint32_t l = (blockIdx.x - uint32_t(n_heavy_blocks)) * blockDim.x + threadIdx.x;
+  if (l >= uint32_t(v.n)) return;
+  const size_t st = size_t(v.stride);
+  const int32_t e[3] = {v.nbr[l], v.nbr[st + l], v.nbr[2 * st + l]};
   const float h = edge_f(v.D, v.level[l]);
   const float ul = ubar[l];
   float g[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const int32_t e = v.nbr[int64_t(d) * v.stride + l];
     float acc = 0.0f;
-    if (e >= 0) {
+    if (e[d] >= 0) {
       // same or coarser neighbour: alpha = 1
-      const float hm = edge_f(v.D, entry_level(e));
-      acc = (ubar[entry_idx(e)] - ul) * inv_delta(h, hm);
-    } else if (e != kEmpty) {
-      const uint32_t st = list_start(e);
-      const int cnt = v.ovf[st];
+      acc = (ubar[entry_idx(e[d])] - ul) * inv_delta(h, edge_f(v.D, entry_level(e[d])));
+    } else if (e[d] != kEmpty) {
+      const uint32_t s0 = list_start(e[d]);
+      const int cnt = v.ovf[s0];
       if (cnt > kHeavy) return;   // updated by a heavy block
       for (int k = 0; k < cnt; ++k) {
-        const int32_t f = v.ovf[st + 1 + k];
+        const int32_t f = v.ovf[s0 + 1 + k];
         const float hm = edge_f(v.D, entry_level(f));
         const float r = hm / h;
         acc += r * r * (ubar[entry_idx(f)] - ul) * inv_delta(h, hm);
@@ -330,100 +331,148 @@ __constant__ double kInvOnePlusPow2[16] = {
     1.0 / 65.0,    1.0 / 129.0,   1.0 / 257.0,   1.0 / 513.0,   1.0 / 1025.0,  1.0 / 2049.0,
     1.0 / 4097.0,  1.0 / 8193.0,  1.0 / 16385.0, 1.0 / 32769.0};
 
+__device__ __forceinline__ double pow2d(int e) {
+  return __longlong_as_double(static_cast<long long>(1023 + e) << 52);   // 2^e, |e| < 1000
+}
+
 // alpha / Delta for the ordered pair (row leaf of edge exponent a, neighbour
-// of edge exponent b) with alpha = min(1, (2^b / 2^a)^2).
+// of edge exponent b) with alpha = min(1, (2^b / 2^a)^2); exact scalings of a
+// table entry by powers of two.
 __device__ __forceinline__ double face_weight(int a, int b) {
   const int lo = a < b ? a : b;
   const int d = a < b ? b - a : a - b;
-  const double inv_delta = ldexp(kInvOnePlusPow2[d], 1 - lo);
-  return b < a ? ldexp(inv_delta, 2 * (b - a)) : inv_delta;
+  const double inv_delta = kInvOnePlusPow2[d] * pow2d(1 - lo);
+  return b < a ? inv_delta * pow2d(2 * (b - a)) : inv_delta;
 }
 
+// Neighbour sums of one leaf's energy terms over one face's entries, split
+// over `nthr` threads starting at `t0` (1 and 0 for a thread, the block for a
+// heavy leaf): for a +face the gradient component and its coefficient sum,
+// for a -face the divergence contribution.
+__device__ __forceinline__ void face_terms(const View& v, const float* __restrict__ u,
+                                           const float* __restrict__ p, int64_t l, int a, double ul,
+                                           int face, int t0, int nthr, double* g, double* coef,
+                                           double* dvm) {
+  const int32_t e = v.nbr[int64_t(face) * v.stride + l];
+  if (e == kEmpty) return;
+  const int32_t* lst = &e;
+  int cnt = 1;
+  if (e < 0) {
+    cnt = v.ovf[list_start(e)];
+    lst = v.ovf + list_start(e) + 1;
+  }
+  const int d = face % 3;
+  for (int k = t0; k < cnt; k += nthr) {
+    const int32_t f = lst[k];
+    const int b = v.D - entry_level(f);
+    if (face < 3) {
+      const double w = face_weight(a, b);
+      *g += w * (double(u[entry_idx(f)]) - ul);
+      *coef += w;
+    } else {
+      // (h_n^3 / h^3) alpha_nl / Delta
+      const double w = face_weight(b, a) * pow2d(3 * (b - a));
+      *dvm += w * double(p[int64_t(d) * v.stride + entry_idx(f)]);
+    }
+  }
+}
+
+// Primal and dual terms of leaf l from its gradient (g2 = |g|^2) and div p.
+template <typename T>
+__device__ __forceinline__ void leaf_terms(const uint32_t* __restrict__ soff,
+                                           const T* __restrict__ samp, int64_t l, int a, double ul,
+                                           double g2, double dv, double lambda, double gamma,
+                                           double* sp, double* sd) {
+  const double vol = pow2d(3 * a);
+  const uint32_t o = soff[l];
+  const int W = int(soff[l + 1] - o);
+  const double rc = 1.0 / (double(W) + gamma);
+  double data = 0.0;
+  for (int k = 0; k < W; ++k) data += fabs(ul - double(load_sample(samp, o + k)));
+  *sp += vol * (rc * data + lambda * sqrt(g2));
+  // dual term: first k with slope c (2k - W) - dv >= 0, i.e. k >= (W + dv / c) / 2
+  double xs;
+  const double kk = ceil((double(W) + dv * (double(W) + gamma)) * 0.5);
+  if (kk <= 0.0) xs = -1.0;
+  else if (kk > double(W)) xs = 1.0;
+  else xs = double(load_sample(samp, o + int(kk) - 1));
+  xs = fmin(1.0, fmax(-1.0, xs));
+  double dd = 0.0;
+  for (int k = 0; k < W; ++k) dd += fabs(xs - double(load_sample(samp, o + k)));
+  *sd += vol * (rc * dd - xs * dv);
+}
+
+__device__ __forceinline__ double block_sum_d(double x, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+  return t;
+}
+
+// Blocks [0, n_heavy_blocks) sum the heavy leaves (one leaf at a time per
+// block, list entries split over the block); the other blocks the light
+// leaves, one per thread.  Each block writes its (primal, dual) partial.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_energy(View v, const float* __restrict__ u,
                                                      const float* __restrict__ p,
                                                      const uint32_t* __restrict__ soff,
                                                      const T* __restrict__ samp, double lambda,
-                                                     double gamma, double* __restrict__ partial) {
+                                                     double gamma, const uint32_t* __restrict__ heavy,
+                                                     int n_heavy, int n_heavy_blocks,
+                                                     double* __restrict__ partial) {
+  __shared__ double red[kThreads / 32];
   double sp = 0.0, sd = 0.0;
-  for (int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; l < v.n;
-       l += int64_t(gridDim.x) * blockDim.x) {
-    const int lev = v.level[l];
-    const int a = v.D - lev;                 // edge exponent
-    const double vol = ldexp(1.0, 3 * a);
-    const double ul = double(u[l]);
-    double g2 = 0.0, dv = 0.0;
-    for (int d = 0; d < 3; ++d) {
-      const int32_t e = v.nbr[int64_t(d) * v.stride + l];
-      double g = 0.0, coef = 0.0;
-      if (e != kEmpty) {
-        const int32_t* lst = &e;
-        int cnt = 1;
-        if (e < 0) {
-          cnt = v.ovf[list_start(e)];
-          lst = v.ovf + list_start(e) + 1;
-        }
-        for (int k = 0; k < cnt; ++k) {
-          const double w = face_weight(a, v.D - entry_level(lst[k]));
-          g += w * (double(u[entry_idx(lst[k])]) - ul);
-          coef += w;
-        }
+  if (int(blockIdx.x) < n_heavy_blocks) {
+    for (int q = blockIdx.x; q < n_heavy; q += n_heavy_blocks) {
+      const int64_t l = heavy[q];
+      const int a = v.D - v.level[l];
+      const double ul = double(u[l]);
+      double g2 = 0.0, dv = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        double g = 0.0, coef = 0.0, dvm = 0.0;
+        face_terms(v, u, p, l, a, ul, d, threadIdx.x, kThreads, &g, &coef, &dvm);
+        face_terms(v, u, p, l, a, ul, 3 + d, threadIdx.x, kThreads, &g, &coef, &dvm);
+        g = block_sum_d(g, red);
+        coef = block_sum_d(coef, red);
+        dvm = block_sum_d(dvm, red);
+        g2 += g * g;
+        dv += coef * double(p[int64_t(d) * v.stride + l]) - dvm;
       }
-      g2 += g * g;
-      dv += coef * double(p[int64_t(d) * v.stride + l]);
-      const int32_t e2 = v.nbr[int64_t(3 + d) * v.stride + l];
-      if (e2 != kEmpty) {
-        const int32_t* lst = &e2;
-        int cnt = 1;
-        if (e2 < 0) {
-          cnt = v.ovf[list_start(e2)];
-          lst = v.ovf + list_start(e2) + 1;
-        }
-        for (int k = 0; k < cnt; ++k) {
-          const int bn = v.D - entry_level(lst[k]);
-          // (h_n^3 / h^3) alpha_nl / Delta
-          const double w = ldexp(face_weight(bn, a), 3 * (bn - a));
-          dv -= w * double(p[int64_t(d) * v.stride + entry_idx(lst[k])]);
-        }
-      }
+      if (threadIdx.x == 0) leaf_terms(soff, samp, l, a, ul, g2, dv, lambda, gamma, &sp, &sd);
     }
-    const uint32_t o = soff[l];
-    const int W = int(soff[l + 1] - o);
-    const double rc = 1.0 / (double(W) + gamma);
-    double data = 0.0;
-    for (int k = 0; k < W; ++k) data += fabs(ul - double(load_sample(samp, o + k)));
-    sp += vol * (rc * data + lambda * sqrt(g2));
-    // dual term: first k with slope c (2k - W) - dv >= 0, i.e. k >= (W + dv / c) / 2
-    double xs;
-    const double kk = ceil((double(W) + dv * (double(W) + gamma)) * 0.5);
-    if (kk <= 0.0) xs = -1.0;
-    else if (kk > double(W)) xs = 1.0;
-    else xs = double(load_sample(samp, o + int(kk) - 1));
-    xs = fmin(1.0, fmax(-1.0, xs));
-    double dd = 0.0;
-    for (int k = 0; k < W; ++k) dd += fabs(xs - double(load_sample(samp, o + k)));
-    sd += vol * (rc * dd - xs * dv);
+  } else {
+    const int nb = int(gridDim.x) - n_heavy_blocks;
+    for (int64_t l = int64_t(blockIdx.x - n_heavy_blocks) * blockDim.x + threadIdx.x; l < v.n;
+         l += int64_t(nb) * blockDim.x) {
+      bool heavy_leaf = false;
+      for (int face = 0; face < 6; ++face) {
+        const int32_t e = v.nbr[int64_t(face) * v.stride + l];
+        heavy_leaf |= is_list(e) && v.ovf[list_start(e)] > kHeavy;
+      }
+      if (heavy_leaf) continue;   // summed by a heavy block
+      const int a = v.D - v.level[l];
+      const double ul = double(u[l]);
+      double g2 = 0.0, dv = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        double g = 0.0, coef = 0.0, dvm = 0.0;
+        face_terms(v, u, p, l, a, ul, d, 0, 1, &g, &coef, &dvm);
+        face_terms(v, u, p, l, a, ul, 3 + d, 0, 1, &g, &coef, &dvm);
+        g2 += g * g;
+        dv += coef * double(p[int64_t(d) * v.stride + l]) - dvm;
+      }
+      leaf_terms(soff, samp, l, a, ul, g2, dv, lambda, gamma, &sp, &sd);
+    }
   }
-  __shared__ double rp[kThreads / 32], rd[kThreads / 32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    sp += __shfl_xor_sync(kFull, sp, o);
-    sd += __shfl_xor_sync(kFull, sd, o);
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) {
-    rp[wid] = sp;
-    rd[wid] = sd;
-  }
-  __syncthreads();
+  // block partial in a fixed order
+  const double bp = block_sum_d(sp, red);
+  const double bd = block_sum_d(sd, red);
   if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) {
-      a += rp[w];
-      b += rd[w];
-    }
-    partial[2 * blockIdx.x] = a;
-    partial[2 * blockIdx.x + 1] = b;
+    partial[2 * blockIdx.x] = bp;
+    partial[2 * blockIdx.x + 1] = bd;
   }
 }
 
@@ -499,17 +548,24 @@ cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const f
 
 size_t energy_tmp_bytes(int64_t) { return size_t(2 * kEnergyBlocks) * sizeof(double); }
 
+// Heavy leaves get min(n_heavy, kEnergyHeavyBlocks) blocks at the front of
+// the grid; light leaves up to kEnergyBlocks - that many.
+constexpr int kEnergyHeavyBlocks = 256;
+
 cudaError_t launch_energy(View v, const float* u, const float* p, const uint32_t* soff,
                           const void* samp, bool fp16, double lambda, double gamma,
-                          double* partial, double* out3, cudaStream_t s) {
+                          const uint32_t* heavy, int n_heavy, double* partial, double* out3,
+                          cudaStream_t s) {
+  const int hb = n_heavy < kEnergyHeavyBlocks ? n_heavy : kEnergyHeavyBlocks;
   const int64_t want = (v.n + kThreads - 1) / kThreads;
-  const int nb = int(want < 1 ? 1 : (want < kEnergyBlocks ? want : kEnergyBlocks));
+  const int lb = int(want < 1 ? 1 : (want < kEnergyBlocks - hb ? want : kEnergyBlocks - hb));
+  const int nb = hb + lb;
   if (fp16)
     k_energy<__half><<<nb, kThreads, 0, s>>>(v, u, p, soff, reinterpret_cast<const __half*>(samp),
-                                             lambda, gamma, partial);
+                                             lambda, gamma, heavy, n_heavy, hb, partial);
   else
     k_energy<float><<<nb, kThreads, 0, s>>>(v, u, p, soff, reinterpret_cast<const float*>(samp),
-                                            lambda, gamma, partial);
+                                            lambda, gamma, heavy, n_heavy, hb, partial);
   count_launches(1);
   k_energy_final<<<1, kFinalThreads, 0, s>>>(partial, nb, out3);
   count_launches(1);
@@ -555,16 +611,19 @@ cudaError_t energy_static_scratch(double** ptr) {
 
 cudaError_t launch_energy_static(View v, const float* u, const float* p, const uint32_t* soff,
                                  const void* samp, bool fp16, double lambda, double gamma,
-                                 double* scratch, cudaStream_t s) {
+                                 const uint32_t* heavy, int n_heavy, double* scratch,
+                                 cudaStream_t s) {
   const int64_t want = (v.n + kStaticLeavesPerBlock - 1) / kStaticLeavesPerBlock;
   if (want > kStaticEnergyBlocks) return cudaErrorInvalidValue;
-  const int nb = want < 1 ? 1 : int(want);
+  const int hb = n_heavy < kEnergyHeavyBlocks ? n_heavy : kEnergyHeavyBlocks;
+  const int lb = want < 1 ? 1 : int(want);
+  const int nb = lb + hb <= kStaticEnergyBlocks ? lb + hb : kStaticEnergyBlocks;
   if (fp16)
     k_energy<__half><<<nb, kThreads, 0, s>>>(v, u, p, soff, reinterpret_cast<const __half*>(samp),
-                                             lambda, gamma, scratch);
+                                             lambda, gamma, heavy, n_heavy, hb, scratch);
   else
     k_energy<float><<<nb, kThreads, 0, s>>>(v, u, p, soff, reinterpret_cast<const float*>(samp),
-                                            lambda, gamma, scratch);
+                                            lambda, gamma, heavy, n_heavy, hb, scratch);
   count_launches(1);
   k_energy_final<<<1, kFinalThreads, 0, s>>>(scratch, nb, scratch + 2 * kStaticEnergyBlocks);
   count_launches(1);
