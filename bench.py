@@ -270,6 +270,20 @@ def time_to_energy(a, scene, of, stream, depth_d, intr_d, pose_d):
     return out
 
 
+def aggregate(dist, total_ms, work, device):
+    """Whole-job figures of a multi-rank run: the step time is the slowest
+    rank's, the work (leaf-iterations) the sum over ranks.  Without a process
+    group the rank's own values are returned."""
+    if dist is None:
+        return float(total_ms), float(work)
+    import torch
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([work], dtype=torch.float64, device=device)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
 def main():
     a = args_()
     rank = int(os.environ.get("RANK", "0"))
@@ -354,16 +368,7 @@ def main():
     clk = clocks.stop()
     n_final = of.ofu_num_leaves(ctx)
     n_samples = of.ofu_export_field(ctx, of.FIELD_SAMPLES, None, 0)
-    total_ms = sum(times)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        li_t = torch.tensor([leaf_iters], dtype=torch.float64, device=dev)
-        dist.all_reduce(li_t)
-        leaf_iters_all = float(li_t.item())
-    else:
-        leaf_iters_all = float(leaf_iters)
+    total_ms, leaf_iters_all = aggregate(dist, sum(times), leaf_iters, dev)
     value = leaf_iters_all / (total_ms / 1e3)
 
     # ---- end to end through the C ABI with pinned host buffers ----
@@ -387,13 +392,7 @@ def main():
         e2e_t.append(time.perf_counter() - t0)
         e2e_li += li
         d2h = n * (8 + 1 + 4) + 24
-    e2e_total = sum(e2e_t)
-    if dist:
-        t = torch.tensor([e2e_total, e2e_li], dtype=torch.float64, device=dev)
-        t0_ = t.clone()
-        dist.all_reduce(t0_[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:])
-        e2e_total, e2e_li = float(t0_[0].item()), float(t[1].item())
+    e2e_total, e2e_li = aggregate(dist, sum(e2e_t), e2e_li, dev)
     e2e_val = e2e_li / e2e_total
     h2d = scene.depth.nbytes + scene.intr.nbytes + scene.pose.nbytes
 

@@ -194,6 +194,22 @@ ofu_status ofu_import_leaves(ofu_ctx* ctx, const uint64_t* keys, const uint8_t* 
  * may be NULL for ubar = u) on the current structure. */
 ofu_status ofu_set_state(ofu_ctx* ctx, const float* u, const float* ubar, const float* p, int64_t n);
 
+/* ---- checkpoint / resume ------------------------------------------------- */
+
+/* Writes the context to a file: parameters, the frames (as the range maps
+ * the integration uses) and cameras, the leaves (keys, levels) and the
+ * iterate (u, ubar, p).  Synchronises the stream.  EINVAL if the file cannot
+ * be written. */
+ofu_status ofu_save(ofu_ctx* ctx, const char* path);
+
+/* Restores a file written by ofu_save into `ctx` (created with any
+ * parameters; they are replaced by the file's).  Samples, neighbours and
+ * step sizes are rebuilt from the stored frames and leaves, so iterating
+ * after a load gives bit for bit what the saved context would have given.
+ * EINVAL for a missing or malformed file (the context is then without an
+ * octree). */
+ofu_status ofu_load(ofu_ctx* ctx, const char* path);
+
 /* ---- learned warm start (not in the paper) ----------------------------- */
 /*
  * A per-leaf network replaces the median initialisation of observed leaves

@@ -195,24 +195,27 @@ ofu_status rebuild_topology(ofu_ctx* ctx, const uint32_t* samples_total = nullpt
     ctx->heavy_cap = cap;
   }
   unsigned long long* nlong = reinterpret_cast<unsigned long long*>(small + 8);
-  unsigned long long* hcount = reinterpret_cast<unsigned long long*>(small + 9);
+  uint64_t *hflags, *htmp;
+  ST(ensure(ctx, B_CLS, size_t(n + 1), &hflags));
+  ST(ensure(ctx, B_OUTC, scan_tmp_items<uint64_t>(n) * 2, &htmp));
   Leaves& L = ctx->L[ctx->cur];
   View v = view_of(ctx);
   CU(launch_nbr_count(v, L.nbr, ovfc, longq, nlong, ctx->stream));
-  CU(launch_heavy(v, ovfc, ctx->heavy, ctx->heavy + ctx->heavy_cap, hcount, ctx->stream));
+  CU(launch_heavy(v, ovfc, hflags, htmp, ctx->heavy, ctx->heavy + ctx->heavy_cap, ctx->stream));
   CU(scan_exclusive<uint32_t>(ovfc, ovfc, 6 * n, tmp, ctx->stream));
-  // one read-back: [list total (u32), samples (u32)] in slot 11, heavy counts in 9, 10
-  CU(cudaMemcpyAsync(reinterpret_cast<uint32_t*>(small + 11), ovfc + 6 * n, sizeof(uint32_t),
+  // one read-back: packed heavy counts (slot 9), [list total, samples] (slot 10)
+  CU(cudaMemcpyAsync(small + 9, hflags + n, sizeof(uint64_t), cudaMemcpyDeviceToDevice, ctx->stream));
+  CU(cudaMemcpyAsync(reinterpret_cast<uint32_t*>(small + 10), ovfc + 6 * n, sizeof(uint32_t),
                      cudaMemcpyDeviceToDevice, ctx->stream));
   if (samples_total)
-    CU(cudaMemcpyAsync(reinterpret_cast<uint32_t*>(small + 11) + 1, samples_total, sizeof(uint32_t),
+    CU(cudaMemcpyAsync(reinterpret_cast<uint32_t*>(small + 10) + 1, samples_total, sizeof(uint32_t),
                        cudaMemcpyDeviceToDevice, ctx->stream));
-  uint64_t hs[3];
-  ST(read_back(ctx, small + 9, 3 * sizeof(uint64_t), hs));
-  ctx->n_heavy_dual = int(hs[0]);
-  ctx->n_heavy_primal = int(hs[1]);
-  const uint32_t total = uint32_t(hs[2] & 0xffffffffu);
-  if (samples_total) ctx->n_samples = int64_t(hs[2] >> 32);
+  uint64_t hs[2];
+  ST(read_back(ctx, small + 9, 2 * sizeof(uint64_t), hs));
+  ctx->n_heavy_dual = int(hs[0] & 0xffffffffu);
+  ctx->n_heavy_primal = int(hs[0] >> 32);
+  const uint32_t total = uint32_t(hs[1] & 0xffffffffu);
+  if (samples_total) ctx->n_samples = int64_t(hs[1] >> 32);
   if (int64_t(total) + 1 > ctx->ovf_cap) {
     if (ctx->ovf) CU(cudaFree(ctx->ovf));
     ctx->ovf = nullptr;
@@ -954,6 +957,107 @@ ofu_status ofu_warm_start(ofu_ctx* ctx, const ofu_mlp* net) {
   // dual start consistent with the new field: lambda n on its edges
   CU(launch_dual_init(view_of(ctx), L.u, L.p, float(ctx->prm.lambda), kWarmEdge, ctx->heavy,
                       ctx->n_heavy_dual, ctx->stream));
+  return OFU_OK;
+}
+
+// ---- checkpoint -------------------------------------------------------------
+
+namespace {
+const char kCkptMagic[8] = {'O', 'F', 'U', 'C', 'K', 'P', 'T', '1'};
+
+bool put(FILE* f, const void* p, size_t n) { return n == 0 || std::fwrite(p, 1, n, f) == n; }
+bool get(FILE* f, void* p, size_t n) { return n == 0 || std::fread(p, 1, n, f) == n; }
+}  // namespace
+
+ofu_status ofu_save(ofu_ctx* ctx, const char* path) {
+  ST(check_built(ctx));
+  if (!path) return fail(ctx, OFU_EINVAL, "save: path is NULL");
+  const int64_t n = ctx->n;
+  const size_t fr = size_t(ctx->F) * ctx->H * ctx->W;
+  Leaves& L = ctx->L[ctx->cur];
+  std::vector<float> rmap(fr), u(n), ub(n), p(3 * size_t(n));
+  std::vector<Cam> cams(ctx->F);
+  std::vector<uint64_t> keys(n);
+  std::vector<uint8_t> lv(n);
+  cudaStream_t s = ctx->stream;
+  CU(cudaMemcpyAsync(rmap.data(), ctx->depth, fr * 4, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(cams.data(), ctx->cams, cams.size() * sizeof(Cam), cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(keys.data(), L.key, n * 8, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(lv.data(), L.level, n, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(u.data(), L.u, n * 4, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(ub.data(), L.ubar, n * 4, cudaMemcpyDeviceToHost, s));
+  for (int d = 0; d < 3; ++d)
+    CU(cudaMemcpyAsync(p.data() + d * n, L.p + d * L.cap, n * 4, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(ctx, OFU_EINVAL, std::string("save: cannot open ") + path);
+  const int32_t dims[3] = {ctx->F, ctx->H, ctx->W};
+  bool ok = put(f, kCkptMagic, 8) && put(f, &ctx->prm, sizeof(ofu_params)) && put(f, dims, 12) &&
+            put(f, cams.data(), cams.size() * sizeof(Cam)) && put(f, rmap.data(), fr * 4) &&
+            put(f, &n, 8) && put(f, keys.data(), n * 8) && put(f, lv.data(), n) &&
+            put(f, u.data(), n * 4) && put(f, ub.data(), n * 4) && put(f, p.data(), 3 * n * 4);
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(ctx, OFU_EINVAL, std::string("save: write failed for ") + path);
+  return OFU_OK;
+}
+
+ofu_status ofu_load(ofu_ctx* ctx, const char* path) {
+  ST(check_ready(ctx));
+  if (!path) return fail(ctx, OFU_EINVAL, "load: path is NULL");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(ctx, OFU_EINVAL, std::string("load: cannot open ") + path);
+  char magic[8];
+  ofu_params prm;
+  int32_t dims[3];
+  int64_t n = 0;
+  bool ok = get(f, magic, 8) && std::memcmp(magic, kCkptMagic, 8) == 0 &&
+            get(f, &prm, sizeof(prm)) && get(f, dims, 12);
+  std::string why;
+  ok = ok && validate(&prm, &why) == OFU_OK && dims[0] >= 1 && dims[0] <= 512 && dims[1] >= 1 &&
+       dims[2] >= 1;
+  std::vector<Cam> cams;
+  std::vector<float> rmap, u, ub, p;
+  std::vector<uint64_t> keys;
+  std::vector<uint8_t> lv;
+  if (ok) {
+    cams.resize(dims[0]);
+    rmap.resize(size_t(dims[0]) * dims[1] * dims[2]);
+    ok = get(f, cams.data(), cams.size() * sizeof(Cam)) && get(f, rmap.data(), rmap.size() * 4) &&
+         get(f, &n, 8) && n >= 1 && n <= kMaxLeaves;
+  }
+  if (ok) {
+    keys.resize(n);
+    lv.resize(n);
+    u.resize(n);
+    ub.resize(n);
+    p.resize(3 * size_t(n));
+    ok = get(f, keys.data(), n * 8) && get(f, lv.data(), n) && get(f, u.data(), n * 4) &&
+         get(f, ub.data(), n * 4) && get(f, p.data(), 3 * n * 4);
+  }
+  std::fclose(f);
+  if (!ok) return fail(ctx, OFU_EINVAL, std::string("load: not a valid checkpoint: ") + path);
+  // frames (range maps) and parameters, then the structure and the iterate
+  ctx->prm = prm;
+  const size_t fr = rmap.size();
+  if (ctx->depth) CU(cudaFree(ctx->depth));
+  if (ctx->cams) CU(cudaFree(ctx->cams));
+  if (ctx->map) CU(cudaFree(ctx->map));
+  ctx->depth = nullptr;
+  ctx->cams = nullptr;
+  ctx->map = nullptr;
+  CU(cudaMalloc(&ctx->depth, fr * 4));
+  CU(cudaMalloc(&ctx->cams, cams.size() * sizeof(Cam)));
+  CU(cudaMemcpy(ctx->depth, rmap.data(), fr * 4, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(ctx->cams, cams.data(), cams.size() * sizeof(Cam), cudaMemcpyHostToDevice));
+  ctx->F = dims[0];
+  ctx->H = dims[1];
+  ctx->W = dims[2];
+  ctx->have_frames = true;
+  ctx->n = 0;
+  ST(ofu_import_leaves(ctx, keys.data(), lv.data(), n, u.data(), p.data()));
+  Leaves& L = ctx->L[ctx->cur];
+  CU(cudaMemcpyAsync(L.ubar, ub.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
   return OFU_OK;
 }
 

@@ -756,9 +756,11 @@ __global__ void k_precond(View v, float* __restrict__ tau, float* __restrict__ s
 }
 
 // Heavy leaves from the list counts of the neighbour pass (1 + list length
-// per list face, 0 otherwise), before those counts are scanned.
-__global__ void k_heavy(View v, const uint32_t* __restrict__ ovf_count, uint32_t* __restrict__ hd,
-                        uint32_t* __restrict__ hp, unsigned long long* __restrict__ counts) {
+// per list face, 0 otherwise), before those counts are scanned: a packed flag
+// per leaf (bit 0 dual-heavy, bit 32 primal-heavy), scanned, then emitted in
+// leaf order, so the lists do not depend on scheduling.
+__global__ void k_heavy_flags(View v, const uint32_t* __restrict__ ovf_count,
+                              uint64_t* __restrict__ flags) {
   const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (l >= v.n) return;
   bool dual = false, primal = false;
@@ -769,8 +771,16 @@ __global__ void k_heavy(View v, const uint32_t* __restrict__ ovf_count, uint32_t
       if (face < 3) dual = true;
     }
   }
-  if (dual) hd[atomicAdd(&counts[0], 1ull)] = uint32_t(l);
-  if (primal) hp[atomicAdd(&counts[1], 1ull)] = uint32_t(l);
+  flags[l] = (dual ? 1ull : 0ull) | (primal ? (1ull << 32) : 0ull);
+}
+
+__global__ void k_heavy_emit(int64_t n, const uint64_t* __restrict__ scan, uint32_t* __restrict__ hd,
+                             uint32_t* __restrict__ hp) {
+  const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (l >= n) return;
+  const uint64_t a = scan[l], b = scan[l + 1];
+  if ((b & 0xffffffffull) != (a & 0xffffffffull)) hd[a & 0xffffffffull] = uint32_t(l);
+  if ((b >> 32) != (a >> 32)) hp[a >> 32] = uint32_t(l);
 }
 
 __global__ void k_check_tiling(const uint64_t* __restrict__ key, const uint8_t* __restrict__ level,
@@ -1243,11 +1253,14 @@ cudaError_t launch_precond(View v, float* tau, float* sigma, const uint32_t* hea
   return cudaGetLastError();
 }
 
-cudaError_t launch_heavy(View v, const uint32_t* ovf_count, uint32_t* heavy_dual,
-                         uint32_t* heavy_primal, unsigned long long* counts, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s);
-  if (e != cudaSuccess || v.n <= 0) return e;
-  k_heavy<<<blocks_for(v.n, 256), 256, 0, s>>>(v, ovf_count, heavy_dual, heavy_primal, counts);
+cudaError_t launch_heavy(View v, const uint32_t* ovf_count, uint64_t* flags, uint64_t* tmp,
+                         uint32_t* heavy_dual, uint32_t* heavy_primal, cudaStream_t s) {
+  if (v.n <= 0) return cudaSuccess;
+  k_heavy_flags<<<blocks_for(v.n, 256), 256, 0, s>>>(v, ovf_count, flags);
+  count_launches(1);
+  cudaError_t e = scan_exclusive<uint64_t>(flags, flags, v.n, tmp, s);
+  if (e != cudaSuccess) return e;
+  k_heavy_emit<<<blocks_for(v.n, 256), 256, 0, s>>>(v.n, flags, heavy_dual, heavy_primal);
   count_launches(1);
   return cudaGetLastError();
 }

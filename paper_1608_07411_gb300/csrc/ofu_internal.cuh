@@ -270,12 +270,13 @@ cudaError_t launch_leaf_fill(const uint64_t* key, const uint8_t* level, const ui
                              void* samp, bool fp16, float* u, float* ubar, cudaStream_t s);
 
 // Heavy leaves: dual-heavy when a +face list exceeds kHeavy, primal-heavy
-// when any face list does, read from the unscanned neighbour-list counts
-// (counts[0], counts[1] are atomically appended to).
-cudaError_t launch_heavy(View v, const uint32_t* ovf_count, uint32_t* heavy_dual,
-                         uint32_t* heavy_primal, unsigned long long* counts, cudaStream_t s);
+// when any face list does, read from the unscanned neighbour-list counts and
+// listed in leaf order.  flags: n + 1 scratch words (flags[n] receives the
+// packed totals: dual count low 32 bits, primal count high 32 bits); tmp:
+// scan scratch for n.
+cudaError_t launch_heavy(View v, const uint32_t* ovf_count, uint64_t* flags, uint64_t* tmp,
+                         uint32_t* heavy_dual, uint32_t* heavy_primal, cudaStream_t s);
 
-// Face neighbours (two passes) and step sizes.
 // Face neighbours: count pass (long lists queued in longq and counted by a
 // block each), then the fill.
 cudaError_t launch_nbr_count(View v, int32_t* nbr, uint32_t* ovf_count, uint32_t* longq,

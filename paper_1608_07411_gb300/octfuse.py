@@ -81,6 +81,8 @@ _SIGS = {
     "ofu_features": (_i32, [_vp, _vp, _i64]),
     "ofu_warm_start": (_i32, [_vp, _vp]),
     "ofu_energy_static": (_i32, [_vp, _vp]),
+    "ofu_save": (_i32, [_vp, ctypes.c_char_p]),
+    "ofu_load": (_i32, [_vp, ctypes.c_char_p]),
     "ofu_kernel_launches": (_i64, []),
     "ofu_profile": (_i32, [_vp, _i32]),
     "ofu_profile_read": (_i32, [_vp, _PD, _P64, _PD]),
@@ -285,6 +287,14 @@ def ofu_energy_static(ctx, out3=None):
     return tuple(float(x) for x in out3) if host else out3
 
 
+def ofu_save(ctx, path: str) -> None:
+    _check(ctx, load().ofu_save(ctx, os.fsencode(path)))
+
+
+def ofu_load(ctx, path: str) -> None:
+    _check(ctx, load().ofu_load(ctx, os.fsencode(path)))
+
+
 def ofu_kernel_launches() -> int:
     return int(load().ofu_kernel_launches())
 
@@ -406,3 +416,9 @@ class Octree:
 
     def solve(self, iters, restructure_every=10, check_every=0, gap_tol=0.0):
         return ofu_solve(self.ctx, iters, restructure_every, check_every, gap_tol)
+
+    def save(self, path):
+        ofu_save(self.ctx, path)
+
+    def load(self, path):
+        ofu_load(self.ctx, path)

@@ -346,3 +346,28 @@ def test_full_size_solve_properties(full):
     assert np.all(np.abs(u) <= 1.0)
     assert np.all(np.linalg.norm(p, axis=1) <= scene.lam * (1 + 1e-5))
     assert G >= -1e-9 * abs(P) and G < G0 and P < P0
+
+
+def test_checkpoint_resume_is_bit_identical(tmp_path):
+    """Saving mid-solve and resuming in a fresh context continues exactly as
+    the uninterrupted context does (deterministic kernels, fixed-order sums)."""
+    scene = make_scene("torus_box", 14, frames=12, width=160, height=120, max_depth=6)
+    a = gpu_octree(scene)
+    a.iterate(20)
+    a.restructure()
+    a.iterate(5)
+    path = str(tmp_path / "ckpt.ofu")
+    a.save(path)
+    b = octfuse.Octree(octfuse.ofu_default_params())
+    b.load(path)
+    for o in (a, b):
+        o.iterate(10)
+        o.restructure()
+        o.iterate(10)
+    for x, y in zip(a.leaves(), b.leaves()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.field(octfuse.FIELD_P), b.field(octfuse.FIELD_P))
+    assert a.energy() == b.energy()
+    with pytest.raises(octfuse.OfuError) as e:
+        b.load(str(tmp_path / "missing.ofu"))
+    assert e.value.status == octfuse.OFU_EINVAL
