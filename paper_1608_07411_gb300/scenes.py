@@ -278,6 +278,7 @@ def make_scene(name: str, seed: int = 0, **over) -> Scene:
         z = _render(shapes, pose[i], intr[i], Wd, Hd)
         rng = _frame_rng(seed, i)
         hitm = np.isfinite(z)
+        zf = np.where(hitm, z, 0.0)     # noise is drawn for every pixel, applied to hits
         if name == "sphere":
             z = np.where(hitm, z + rng.normal(0.0, 0.001, z.shape), z)
         elif name == "torus_box":
@@ -285,7 +286,7 @@ def make_scene(name: str, seed: int = 0, **over) -> Scene:
             out = rng.random(z.shape) < 0.01
             z = np.where(out, rng.uniform(0.5, 2.0, z.shape), z)
         else:
-            z = np.where(hitm, z + rng.normal(0.0, 1.0, z.shape) * 0.0015 * z * z, z)
+            z = np.where(hitm, zf + rng.normal(0.0, 1.0, z.shape) * 0.0015 * zf * zf, z)
         depth[i] = z.astype(np.float32)
 
     vox = extent / (1 << int(cfg["max_depth"]))
