@@ -154,6 +154,9 @@ ofu_status read_back(ofu_ctx* ctx, const void* dev, size_t bytes, void* host) {
   return OFU_OK;
 }
 
+// Events of the per-launch timing (3 per iteration: 8192 iterations).
+constexpr size_t kProfEvents = 3 * 8192;
+
 int64_t max_leaves(const ofu_ctx* ctx) {
   return ctx->prm.max_leaves > 0 ? std::min<int64_t>(ctx->prm.max_leaves, kMaxLeaves) : kMaxLeaves;
 }
@@ -443,24 +446,22 @@ ofu_status ofu_iterate(ofu_ctx* ctx, int32_t n) {
   const View v = view_of(ctx);
   const bool h16 = ctx->prm.sample_fp16 != 0;
   for (int k = 0; k < n; ++k) {
+    // events come from a pool created by ofu_profile(ctx, 1); recording stops
+    // (silently) once the pool is used up
+    const bool rec = ctx->prof_on && ctx->prof_used + 3 <= ctx->prof_ev.size();
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    if (ctx->prof_on) {
-      while (ctx->prof_ev.size() < ctx->prof_used + 3) {
-        cudaEvent_t e;
-        CU(cudaEventCreate(&e));
-        ctx->prof_ev.push_back(e);
-      }
+    if (rec) {
       for (int j = 0; j < 3; ++j) ev[j] = ctx->prof_ev[ctx->prof_used + j];
       ctx->prof_used += 3;
       CU(cudaEventRecord(ev[0], ctx->stream));
     }
     CU(launch_dual(v, L.ubar, L.p, L.sigma, float(ctx->prm.lambda), ctx->heavy,
                    ctx->n_heavy_dual, ctx->stream));
-    if (ctx->prof_on) CU(cudaEventRecord(ev[1], ctx->stream));
+    if (rec) CU(cudaEventRecord(ev[1], ctx->stream));
     CU(launch_primal(v, L.u, L.ubar, L.p, L.tau, L.soff, ctx->samp[ctx->cur], h16,
                      float(ctx->prm.gamma), ctx->heavy + ctx->heavy_cap, ctx->n_heavy_primal,
                      ctx->stream));
-    if (ctx->prof_on) {
+    if (rec) {
       CU(cudaEventRecord(ev[2], ctx->stream));
       ctx->prof_launches[0] += 1;
       ctx->prof_launches[1] += 1;
@@ -1065,6 +1066,12 @@ int64_t ofu_kernel_launches(void) { return launches_so_far(); }
 
 ofu_status ofu_profile(ofu_ctx* ctx, int32_t enable) {
   ST(check_ready(ctx));
+  // the event pool is created here, outside any timed work, once per context
+  while (enable && ctx->prof_ev.size() < kProfEvents) {
+    cudaEvent_t e;
+    CU(cudaEventCreate(&e));
+    ctx->prof_ev.push_back(e);
+  }
   ctx->prof_on = enable != 0;
   if (enable) {
     ctx->prof_used = 0;
