@@ -26,7 +26,7 @@ thread_local std::string g_create_error;
 // Persistent device buffers by role (content not kept across growth).
 enum Buf {
   B_SCAN, B_U0, B_PYR, B_FLAGS, B_POS, B_CNT, B_OVFC, B_CLS, B_OUTC, B_JL, B_SRC, B_LIST,
-  B_SMALL, B_PART, B_BIG, B_LONGQ, B_NUM
+  B_SMALL, B_PART, B_BIG, B_LONGQ, B_FWD, B_AUX, B_FULL, B_NUM
 };
 
 struct Bufs {
@@ -89,6 +89,7 @@ void free_leaves(Leaves& L) {
   cudaFree(L.sigma);
   cudaFree(L.nbr);
   cudaFree(L.soff);
+  cudaFree(L.ovf);
   L = Leaves{};
 }
 
@@ -130,7 +131,7 @@ View view_of(const ofu_ctx* ctx) {
   v.key = L.key;
   v.level = L.level;
   v.nbr = L.nbr;
-  v.ovf = ctx->ovf;
+  v.ovf = L.ovf;
   v.stride = L.cap;
   v.map = ctx->map;
   return v;
@@ -178,7 +179,10 @@ ofu_status rebuild_map(ofu_ctx* ctx) {
 // Voxel map, face neighbours, heavy leaves and step sizes of the current
 // structure.  One host synchronisation (the size of the neighbour lists, the
 // heavy-leaf counts and, when `samples_total` is given, the sample count).
-ofu_status rebuild_topology(ofu_ctx* ctx, const uint32_t* samples_total = nullptr) {
+// With `carry` (the structure before a split/join pass) the entries of kept
+// leaves among kept neighbours are carried over instead of searched.
+ofu_status rebuild_topology(ofu_ctx* ctx, const uint32_t* samples_total = nullptr,
+                            Carry carry = Carry{}) {
   const int64_t n = ctx->n;
   ST(rebuild_map(ctx));
   uint32_t* ovfc;
@@ -201,9 +205,13 @@ ofu_status rebuild_topology(ofu_ctx* ctx, const uint32_t* samples_total = nullpt
   uint64_t *hflags, *htmp;
   ST(ensure(ctx, B_CLS, size_t(n + 1), &hflags));
   ST(ensure(ctx, B_OUTC, scan_tmp_items<uint64_t>(n) * 2, &htmp));
+  if (carry.nbr) {
+    ST(ensure(ctx, B_AUX, size_t(6 * n), &carry.aux));
+    ST(ensure(ctx, B_FULL, size_t(6 * n), &carry.full));
+  }
   Leaves& L = ctx->L[ctx->cur];
   View v = view_of(ctx);
-  CU(launch_nbr_count(v, L.nbr, ovfc, longq, nlong, ctx->stream));
+  CU(launch_nbr_count(v, carry, L.nbr, ovfc, longq, nlong, ctx->stream));
   CU(launch_heavy(v, ovfc, hflags, htmp, ctx->heavy, ctx->heavy + ctx->heavy_cap, ctx->stream));
   CU(scan_exclusive<uint32_t>(ovfc, ovfc, 6 * n, tmp, ctx->stream));
   // one read-back: packed heavy counts (slot 9), [list total, samples] (slot 10)
@@ -219,18 +227,19 @@ ofu_status rebuild_topology(ofu_ctx* ctx, const uint32_t* samples_total = nullpt
   ctx->n_heavy_primal = int(hs[0] >> 32);
   const uint32_t total = uint32_t(hs[1] & 0xffffffffu);
   if (samples_total) ctx->n_samples = int64_t(hs[1] >> 32);
-  if (int64_t(total) + 1 > ctx->ovf_cap) {
-    if (ctx->ovf) CU(cudaFree(ctx->ovf));
-    ctx->ovf = nullptr;
+  if (int64_t(total) + 1 > L.ovf_cap) {
+    if (L.ovf) CU(cudaFree(L.ovf));
+    L.ovf = nullptr;
+    L.ovf_cap = 0;
     const int64_t cap = std::max<int64_t>(int64_t(total) + int64_t(total) / 4 + 1, 1024);
     if (cap >= 0x7fffffffLL) return fail(ctx, OFU_ECAPACITY, "neighbour lists exceed 2^31 entries");
-    CU(cudaMalloc(&ctx->ovf, size_t(cap) * sizeof(int32_t)));
-    ctx->ovf_cap = cap;
+    CU(cudaMalloc(&L.ovf, size_t(cap) * sizeof(int32_t)));
+    L.ovf_cap = cap;
   }
   v = view_of(ctx);
-  CU(launch_nbr_fill(v, ovfc, L.nbr, ctx->ovf, longq, nlong, ctx->stream));
+  CU(launch_nbr_fill(v, carry, ovfc, L.nbr, L.ovf, longq, nlong, ctx->stream));
   v = view_of(ctx);
-  CU(launch_precond(v, L.tau, L.sigma, ctx->heavy + ctx->heavy_cap, ctx->n_heavy_primal,
+  CU(launch_precond(v, carry, L.tau, L.sigma, ctx->heavy + ctx->heavy_cap, ctx->n_heavy_primal,
                     ctx->stream));
   return OFU_OK;
 }
@@ -345,7 +354,6 @@ void ofu_destroy(ofu_ctx* ctx) {
   free_leaves(ctx->L[1]);
   cudaFree(ctx->samp[0]);
   cudaFree(ctx->samp[1]);
-  cudaFree(ctx->ovf);
   cudaFree(ctx->depth);
   cudaFree(ctx->cams);
   cudaFree(ctx->map);
@@ -515,9 +523,11 @@ ofu_status ofu_restructure(ofu_ctx* ctx, int64_t* n_split, int64_t* n_join, int6
   tmp32 = reinterpret_cast<uint32_t*>(tmp64);
   v = view_of(ctx);
   uint32_t* big;
+  int32_t* fwd;
   ST(ensure(ctx, B_BIG, size_t(n), &big));
-  CU(launch_emit(v, L.u, L.p, outc, jl, N2.key, N2.level, N2.u, N2.ubar, N2.p, N2.cap, src, big,
-                 reinterpret_cast<unsigned long long*>(small + 4), ctx->stream));
+  ST(ensure(ctx, B_FWD, size_t(n), &fwd));
+  CU(launch_emit(v, L.u, L.p, outc, jl, N2.key, N2.level, N2.u, N2.ubar, N2.p, N2.cap, src, fwd,
+                 big, reinterpret_cast<unsigned long long*>(small + 4), ctx->stream));
   // new leaves (split children, joined nodes) are listed on the device and
   // integrated without a host round trip; the sample buffer is sized for the
   // worst case (every frame observes every new leaf)
@@ -535,10 +545,18 @@ ofu_status ofu_restructure(ofu_ctx* ctx, int64_t* n_split, int64_t* n_join, int6
                               ctx->stream));
   CU(launch_leaf_fill(N2.key, N2.level, list, nlist, n_new, ctx->depth, ctx->cams, ctx->F, ctx->H,
                       ctx->W, g, N2.soff, ctx->samp[nx], h16, nullptr, nullptr, ctx->stream));
+  Carry carry;
+  carry.nbr = L.nbr;
+  carry.ovf = L.ovf;
+  carry.stride = L.cap;
+  carry.src = src;
+  carry.fwd = fwd;
+  carry.tau = L.tau;
+  carry.sigma = L.sigma;
   ctx->cur = nx;
   ctx->n = n_new;
   (void)D;
-  ST(rebuild_topology(ctx, N2.soff + n_new));
+  ST(rebuild_topology(ctx, N2.soff + n_new, carry));
   if (n_split) *n_split = ns;
   if (n_join) *n_join = nj;
   if (n_leaves) *n_leaves = n_new;
@@ -680,8 +698,8 @@ ofu_status ofu_export_neighbours(ofu_ctx* ctx, int32_t face, int64_t* off, int64
   Leaves& L = ctx->L[ctx->cur];
   std::vector<int32_t> e(n);
   CU(cudaMemcpyAsync(e.data(), L.nbr + int64_t(face) * L.cap, n * 4, cudaMemcpyDeviceToHost, ctx->stream));
-  std::vector<int32_t> ov(ctx->ovf_cap > 0 ? size_t(ctx->ovf_cap) : 0);
-  if (!ov.empty()) CU(cudaMemcpyAsync(ov.data(), ctx->ovf, ov.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  std::vector<int32_t> ov(L.ovf_cap > 0 ? size_t(L.ovf_cap) : 0);
+  if (!ov.empty()) CU(cudaMemcpyAsync(ov.data(), L.ovf, ov.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
   std::vector<int64_t> ho(n + 1), hx;
   ho[0] = 0;

@@ -13,13 +13,25 @@ constexpr unsigned kFull = 0xffffffffu;
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 // ---------------------------------------------------------------------------
-// Prefix sums: tiles of kTile items; one pass of tile totals, a recursive
-// exclusive scan of the totals, then a pass that scans each tile in shared
-// memory and adds its tile offset.
+// Prefix sums: tiles of kTile items.  One pass writes the tile totals; a
+// second pass scans each tile in shared memory and adds its tile offset,
+// which each block sums itself from the totals before it when there are at
+// most kSelfOffsetTiles tiles (two launches in all), else takes from a
+// recursive exclusive scan of the totals.
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kTile = kScanThreads * kScanItems;
+constexpr int kSelfOffsetTiles = 2048;
+
+// Shared-memory slot of tile item i: one pad slot every 32 (4-byte) or 16
+// (8-byte) items keeps both the coalesced-order and the thread-order
+// accesses free of bank conflicts.
+template <typename T>
+__device__ __forceinline__ int tile_slot(int i) {
+  return i + (i >> (sizeof(T) == 8 ? 4 : 5));
+}
+constexpr int kTileSlots = kTile + kTile / 16;
 
 template <typename T>
 __device__ T warp_inclusive(T v) {
@@ -68,32 +80,42 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_sums(const T* __restrict_
   if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
+// offs == nullptr: a single tile.  self_offset: offs holds the tile totals
+// and the block adds those of the tiles before it; else offs[b] is the
+// tile's offset.
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const T* in, T* out, int64_t n,
-                                                            const T* __restrict__ offs) {
-  __shared__ T tile[kTile];
+                                                            const T* __restrict__ offs,
+                                                            int self_offset) {
+  __shared__ T tile[kTileSlots];
   const int64_t base = int64_t(blockIdx.x) * kTile;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     const int idx = k * kScanThreads + threadIdx.x;
     const int64_t i = base + idx;
-    tile[idx] = i < n ? in[i] : T(0);
+    tile[tile_slot<T>(idx)] = i < n ? in[i] : T(0);
   }
-  __syncthreads();
+  T off = 0;
+  if (offs && self_offset) {
+    T acc = 0;
+    for (int b = threadIdx.x; b < int(blockIdx.x); b += kScanThreads) acc += offs[b];
+    block_exclusive(acc, &off);  // synchronises the block, so the tile is loaded
+  } else {
+    if (offs) off = offs[blockIdx.x];
+    __syncthreads();
+  }
   T loc[kScanItems];
   T s = 0;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    loc[k] = tile[threadIdx.x * kScanItems + k];
+    loc[k] = tile[tile_slot<T>(threadIdx.x * kScanItems + k)];
     s += loc[k];
   }
   T tot;
-  T run = block_exclusive(s, &tot);
-  const T off = offs ? offs[blockIdx.x] : T(0);
-  run += off;
+  T run = block_exclusive(s, &tot) + off;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    tile[threadIdx.x * kScanItems + k] = run;
+    tile[tile_slot<T>(threadIdx.x * kScanItems + k)] = run;
     run += loc[k];
   }
   __syncthreads();
@@ -101,7 +123,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const T* in, T* out,
   for (int k = 0; k < kScanItems; ++k) {
     const int idx = k * kScanThreads + threadIdx.x;
     const int64_t i = base + idx;
-    if (i < n) out[i] = tile[idx];
+    if (i < n) out[i] = tile[tile_slot<T>(idx)];
   }
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = off + tot;
 }
@@ -527,18 +549,68 @@ __device__ __forceinline__ int64_t face_rep(const View& v, const FaceSquare& q, 
 // larger ones by a block (k_nbr_long_*).
 constexpr uint32_t kThreadSquare = 16;
 
-// Entry of a face whose finer-neighbour list is not yet written.
+// Entry of a face whose finer-neighbour list is not yet written, and of one
+// whose list is carried over from the structure before a split/join pass.
 constexpr int32_t kListPending = int32_t(0x80000000u | 0x7ffffffeu);
+constexpr int32_t kCarryPending = int32_t(0x80000000u | 0x7ffffffdu);
+// Queue bit of a long list that may be carried; aux values of such a list
+// when it is not carried (searched again) or no longer a list.
+constexpr uint32_t kCarryBit = 0x80000000u;
+constexpr uint32_t kSearch = 0xffffffffu;
+constexpr uint32_t kNotList = 0xfffffffeu;
 
-// One thread per (leaf, face).  Single neighbours and boundaries are final
-// here; finer lists are counted (small squares by this thread, larger ones
-// queued for a block) and marked pending for the fill pass.
-__global__ void k_nbr_count(View v, int32_t* __restrict__ nbr, uint32_t* __restrict__ ovf_count,
-                            uint32_t* __restrict__ longq, unsigned long long* __restrict__ nlong) {
+// One thread per (leaf, face).  Entries carried from the old structure and
+// single neighbours and boundaries are final here; finer lists are counted
+// (small squares and short carried lists by this thread, larger ones queued
+// for a block) and marked pending for the fill pass.  With a carry,
+// cy.full[t] = 1 when the face was carried here.
+__global__ void k_nbr_count(View v, Carry cy, int32_t* __restrict__ nbr,
+                            uint32_t* __restrict__ ovf_count, uint32_t* __restrict__ longq,
+                            unsigned long long* __restrict__ nlong) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= 6 * v.n) return;
   const int face = int(t / v.n);
   const int64_t l = t - int64_t(face) * v.n;
+  const int64_t slot = int64_t(face) * v.stride + l;
+  if (cy.nbr) {
+    const int32_t s = cy.src[l];
+    uint8_t carried = 0;
+    if (s >= 0) {
+      const int32_t eo = cy.nbr[int64_t(face) * cy.stride + s];
+      if (eo == kEmpty) {  // the domain boundary does not move
+        nbr[slot] = kEmpty;
+        ovf_count[t] = 0;
+        carried = 1;
+      } else if (is_single(eo)) {
+        const int32_t m = cy.fwd[entry_idx(eo)];
+        if (m >= 0) {
+          nbr[slot] = make_single(uint32_t(m), entry_level(eo));
+          ovf_count[t] = 0;
+          carried = 1;
+        }
+      } else {
+        const uint32_t so = list_start(eo);
+        const uint32_t c = uint32_t(cy.ovf[so]);
+        if (c > kThreadSquare) {
+          nbr[slot] = kListPending;
+          ovf_count[t] = 1;  // k_nbr_long_count decides
+          longq[atomicAdd(nlong, 1ull)] = uint32_t(t) | kCarryBit;
+          cy.full[t] = 0;
+          return;
+        }
+        bool all = true;
+        for (uint32_t k = 0; k < c; ++k) all &= cy.fwd[entry_idx(cy.ovf[so + 1 + k])] >= 0;
+        if (all) {
+          nbr[slot] = kCarryPending;
+          cy.aux[t] = so;
+          ovf_count[t] = 1 + c;
+          carried = 1;
+        }
+      }
+    }
+    cy.full[t] = carried;
+    if (carried) return;
+  }
   const FaceHit f = face_query(v, l, face);
   int32_t e = kEmpty;
   uint32_t cnt = 0;
@@ -555,31 +627,42 @@ __global__ void k_nbr_count(View v, int32_t* __restrict__ nbr, uint32_t* __restr
       for (uint32_t i = 0; i < q.h * q.h; ++i) cnt += face_rep(v, q, i) >= 0;
     }
   }
-  nbr[int64_t(face) * v.stride + l] = e;
+  nbr[slot] = e;
   ovf_count[t] = cnt;
 }
 
-// Writes the finer-neighbour lists of small squares (pending entries only;
-// every other thread returns after one load) and points each pending entry
-// at its list.
-__global__ void k_nbr_fill(View v, const uint32_t* __restrict__ ovf_off, int32_t* __restrict__ nbr,
-                           int32_t* __restrict__ ovf) {
+// Writes the finer-neighbour lists of small squares and short carried lists
+// (pending entries only; every other thread returns after one load) and
+// points each pending entry at its list.
+__global__ void k_nbr_fill(View v, Carry cy, const uint32_t* __restrict__ ovf_off,
+                           int32_t* __restrict__ nbr, int32_t* __restrict__ ovf) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= 6 * v.n) return;
   const int face = int(t / v.n);
   const int64_t l = t - int64_t(face) * v.n;
   const int64_t slot = int64_t(face) * v.stride + l;
-  if (nbr[slot] != kListPending) return;
+  const int32_t e = nbr[slot];
+  if (e != kListPending && e != kCarryPending) return;
   const uint32_t st = ovf_off[t];
-  const FaceSquare q = face_square(v, l, face);
-  if (q.h * q.h <= kThreadSquare) {
-    uint32_t c = 0;
-#pragma unroll 4
-    for (uint32_t i = 0; i < q.h * q.h; ++i) {
-      const int64_t m = face_rep(v, q, i);
-      if (m >= 0) ovf[st + 1 + c++] = make_single(uint32_t(m), v.level[m]);
+  if (e == kCarryPending) {
+    const uint32_t so = cy.aux[t];
+    const int32_t c = cy.ovf[so];
+    for (int32_t k = 0; k < c; ++k) {
+      const int32_t eo = cy.ovf[so + 1 + k];
+      ovf[st + 1 + k] = make_single(uint32_t(cy.fwd[entry_idx(eo)]), entry_level(eo));
     }
-    ovf[st] = int32_t(c);
+    ovf[st] = c;
+  } else {
+    const FaceSquare q = face_square(v, l, face);
+    if (q.h * q.h <= kThreadSquare) {
+      uint32_t c = 0;
+#pragma unroll 4
+      for (uint32_t i = 0; i < q.h * q.h; ++i) {
+        const int64_t m = face_rep(v, q, i);
+        if (m >= 0) ovf[st + 1 + c++] = make_single(uint32_t(m), v.level[m]);
+      }
+      ovf[st] = int32_t(c);
+    }
   }
   nbr[slot] = make_list(st);
 }
@@ -610,31 +693,85 @@ __device__ uint32_t block_face_walk(const View& v, const FaceSquare& q, Emit emi
   return base;
 }
 
-__global__ void k_nbr_long_count(View v, const uint32_t* __restrict__ longq,
+// Long lists, a block each.  A carry candidate (a kept leaf whose old entry
+// was a long list) keeps its list when every listed leaf was kept; else the
+// face is searched again, and if it no longer has finer neighbours its entry
+// is written here and its aux slot set to kNotList.
+__global__ void k_nbr_long_count(View v, Carry cy, const uint32_t* __restrict__ longq,
                                  const unsigned long long* __restrict__ nlong,
-                                 uint32_t* __restrict__ ovf_count) {
+                                 int32_t* __restrict__ nbr, uint32_t* __restrict__ ovf_count) {
+  __shared__ int kind_s;
+  __shared__ int32_t single_s;
   const unsigned long long nq = *nlong;
   for (unsigned long long j = blockIdx.x; j < nq; j += gridDim.x) {
-    const uint32_t t = longq[j];
+    const uint32_t qv = longq[j];
+    const uint32_t t = qv & ~kCarryBit;
     const int face = int(int64_t(t) / v.n);
     const int64_t l = int64_t(t) - int64_t(face) * v.n;
+    if (qv & kCarryBit) {
+      const int32_t eo = cy.nbr[int64_t(face) * cy.stride + cy.src[l]];
+      const uint32_t so = list_start(eo);
+      const uint32_t c = uint32_t(cy.ovf[so]);
+      int ok = 1;
+      for (uint32_t k = threadIdx.x; k < c; k += blockDim.x)
+        ok &= cy.fwd[entry_idx(cy.ovf[so + 1 + k])] >= 0;
+      if (__syncthreads_and(ok)) {
+        if (threadIdx.x == 0) {
+          ovf_count[t] = 1 + c;
+          cy.aux[t] = so;
+        }
+        continue;
+      }
+      if (threadIdx.x == 0) {
+        const FaceHit f = face_query(v, l, face);
+        kind_s = f.kind;
+        single_s = f.kind == 1 ? make_single(f.m, f.mlev) : kEmpty;
+      }
+      __syncthreads();
+      const int kind = kind_s;
+      const int32_t single = single_s;
+      __syncthreads();
+      if (kind != 2) {
+        if (threadIdx.x == 0) {
+          nbr[int64_t(face) * v.stride + l] = single;
+          ovf_count[t] = 0;
+          cy.aux[t] = kNotList;
+        }
+        continue;
+      }
+      if (threadIdx.x == 0) cy.aux[t] = kSearch;
+    }
     const FaceSquare q = face_square(v, l, face);
     const uint32_t cnt = block_face_walk(v, q, [](uint32_t, int64_t) {});
     if (threadIdx.x == 0) ovf_count[t] = 1 + cnt;
   }
 }
 
-__global__ void k_nbr_long_fill(View v, const uint32_t* __restrict__ longq,
+__global__ void k_nbr_long_fill(View v, Carry cy, const uint32_t* __restrict__ longq,
                                 const unsigned long long* __restrict__ nlong,
                                 const uint32_t* __restrict__ ovf_off, int32_t* __restrict__ ovf) {
   const unsigned long long nq = *nlong;
   for (unsigned long long j = blockIdx.x; j < nq; j += gridDim.x) {
-    const uint32_t t = longq[j];
+    const uint32_t qv = longq[j];
+    const uint32_t t = qv & ~kCarryBit;
     const int face = int(int64_t(t) / v.n);
     const int64_t l = int64_t(t) - int64_t(face) * v.n;
-    const FaceSquare q = face_square(v, l, face);
     const uint32_t st = ovf_off[t];
     int32_t* out = ovf + st + 1;
+    if (qv & kCarryBit) {
+      const uint32_t so = cy.aux[t];
+      if (so == kNotList) continue;
+      if (so != kSearch) {
+        const int32_t c = cy.ovf[so];
+        for (int32_t k = threadIdx.x; k < c; k += blockDim.x) {
+          const int32_t eo = cy.ovf[so + 1 + k];
+          out[k] = make_single(uint32_t(cy.fwd[entry_idx(eo)]), entry_level(eo));
+        }
+        if (threadIdx.x == 0) ovf[st] = c;
+        continue;
+      }
+    }
+    const FaceSquare q = face_square(v, l, face);
     const uint32_t cnt = block_face_walk(v, q, [&](uint32_t pos, int64_t m) {
       out[pos] = make_single(uint32_t(m), v.level[m]);
     });
@@ -693,7 +830,7 @@ __device__ __forceinline__ float block_sum_f(float x, float* red) {
 // alpha = min(1, (h_m / h_l)^2) and centre distance Delta = (h_l + h_m) / 2.
 // Leaves with a list longer than kHeavy get a block each (the first
 // n_heavy blocks); the others a thread.
-__global__ void k_precond(View v, float* __restrict__ tau, float* __restrict__ sigma,
+__global__ void k_precond(View v, Carry cy, float* __restrict__ tau, float* __restrict__ sigma,
                           const uint32_t* __restrict__ heavy, int n_heavy) {
   if (int(blockIdx.x) < n_heavy) {
     __shared__ float red[8];
@@ -730,11 +867,23 @@ __global__ void k_precond(View v, float* __restrict__ tau, float* __restrict__ s
   }
   const int64_t l = int64_t(blockIdx.x - n_heavy) * blockDim.x + threadIdx.x;
   if (l >= v.n) return;
+  if (cy.nbr && cy.full[l] & cy.full[v.n + l] & cy.full[2 * v.n + l] & cy.full[3 * v.n + l] &
+                    cy.full[4 * v.n + l] & cy.full[5 * v.n + l]) {
+    // every face carried: same neighbours and levels as before the pass
+    const int32_t s = cy.src[l];
+    tau[l] = cy.tau[s];
+    sigma[l] = cy.sigma[s];
+    return;
+  }
+  int32_t es[6];
+#pragma unroll
+  for (int face = 0; face < 6; ++face) es[face] = v.nbr[int64_t(face) * v.stride + l];
   const int lev = v.level[l];
   const float hl = pow2f(v.D - lev);
   float rowmax = 0.0f, col = 0.0f;
+#pragma unroll
   for (int face = 0; face < 6; ++face) {
-    const int32_t e = v.nbr[int64_t(face) * v.stride + l];
+    const int32_t e = es[face];
     if (e == kEmpty) continue;
     float row = 0.0f, diag = 0.0f;
     if (is_list(e)) {
@@ -853,30 +1002,36 @@ __global__ void k_mark(View v, const float* __restrict__ u, const uint64_t* __re
 }
 
 constexpr uint64_t kSmallEmit = 64;
+// Joins of more leaves than this are summed by a block (a thread's serial
+// FP64 sum over up to kSmallEmit leaves made the pass wait on one thread).
+constexpr uint64_t kSmallJoin = 8;
 
 // One thread per old leaf writes the new leaves it produces at its offset:
-// kept leaves copy themselves, small splits write their finest children
+// kept leaves copy themselves (and record their new index in fwd; -1 for
+// every other old leaf), small splits write their finest children
 // (inheriting u and p), small joins write the volume-weighted means.  Splits
-// or joins of more than kSmallEmit leaves are queued for k_emit_big.
+// of more than kSmallEmit leaves and joins of more than kSmallJoin leaves are
+// queued for k_emit_big.
 __global__ void k_emit(View v, const float* __restrict__ u, const float* __restrict__ p,
                        const uint64_t* __restrict__ off, const int8_t* __restrict__ join_level,
                        uint64_t* __restrict__ nkey, uint8_t* __restrict__ nlevel,
                        float* __restrict__ nu, float* __restrict__ nubar, float* __restrict__ np_,
-                       int64_t nstride, int32_t* __restrict__ src, uint32_t* __restrict__ big,
-                       unsigned long long* __restrict__ nbig) {
+                       int64_t nstride, int32_t* __restrict__ src, int32_t* __restrict__ fwd,
+                       uint32_t* __restrict__ big, unsigned long long* __restrict__ nbig) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= v.n) return;
   const uint64_t o = off[i];
   const uint64_t oc = off[i + 1] - o;
-  if (oc == 0) return;
   const int jl = join_level[i];
+  fwd[i] = (oc == 1 && jl < 0) ? int32_t(o) : -1;
+  if (oc == 0) return;
   const float ui = u[i];
   const float p0 = p[i], p1 = p[v.stride + i], p2 = p[2 * v.stride + i];
   if (jl >= 0) {
     const uint64_t sz = uint64_t(1) << (3 * (v.D - jl));
     const uint64_t a = v.key[i] & ~(sz - 1);
     const int64_t e = int64_t(v.map[a + sz - 1]) + 1;
-    if (uint64_t(e - i) > kSmallEmit) {
+    if (uint64_t(e - i) > kSmallJoin) {
       big[atomicAdd(nbig, 1ull)] = uint32_t(i);
       return;
     }
@@ -1091,16 +1246,19 @@ size_t scan_tmp_items(int64_t n) {
 template <typename T>
 cudaError_t scan_exclusive(const T* in, T* out, int64_t n, T* tmp, cudaStream_t s) {
   if (n <= kTile) {
-    k_tile_scan<T><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+    k_tile_scan<T><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, 0);
     count_launches(1);
     return cudaGetLastError();
   }
   const int64_t nb = (n + kTile - 1) / kTile;
   k_tile_sums<T><<<unsigned(nb), kScanThreads, 0, s>>>(in, n, tmp);
   count_launches(1);
-  cudaError_t e = scan_exclusive<T>(tmp, tmp, nb, tmp + nb + 1, s);
-  if (e != cudaSuccess) return e;
-  k_tile_scan<T><<<unsigned(nb), kScanThreads, 0, s>>>(in, out, n, tmp);
+  const int self = nb <= kSelfOffsetTiles;
+  if (!self) {
+    cudaError_t e = scan_exclusive<T>(tmp, tmp, nb, tmp + nb + 1, s);
+    if (e != cudaSuccess) return e;
+  }
+  k_tile_scan<T><<<unsigned(nb), kScanThreads, 0, s>>>(in, out, n, tmp, self);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1222,33 +1380,33 @@ cudaError_t launch_leaf_fill(const uint64_t* key, const uint8_t* level, const ui
               : leaf_fill_t<float>(key, level, list, nlist, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
 }
 
-cudaError_t launch_nbr_count(View v, int32_t* nbr, uint32_t* ovf_count, uint32_t* longq,
+cudaError_t launch_nbr_count(View v, Carry cy, int32_t* nbr, uint32_t* ovf_count, uint32_t* longq,
                              unsigned long long* nlong, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(nlong, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k_nbr_count<<<blocks_for(6 * v.n, 256), 256, 0, s>>>(v, nbr, ovf_count, longq, nlong);
+  k_nbr_count<<<blocks_for(6 * v.n, 256), 256, 0, s>>>(v, cy, nbr, ovf_count, longq, nlong);
   count_launches(1);
-  k_nbr_long_count<<<unsigned(sm_count() * 8), 256, 0, s>>>(v, longq, nlong, ovf_count);
+  k_nbr_long_count<<<unsigned(sm_count() * 8), 256, 0, s>>>(v, cy, longq, nlong, nbr, ovf_count);
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_nbr_fill(View v, const uint32_t* ovf_off, int32_t* nbr, int32_t* ovf,
+cudaError_t launch_nbr_fill(View v, Carry cy, const uint32_t* ovf_off, int32_t* nbr, int32_t* ovf,
                             const uint32_t* longq, const unsigned long long* nlong,
                             cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
-  k_nbr_fill<<<blocks_for(6 * v.n, 256), 256, 0, s>>>(v, ovf_off, nbr, ovf);
+  k_nbr_fill<<<blocks_for(6 * v.n, 256), 256, 0, s>>>(v, cy, ovf_off, nbr, ovf);
   count_launches(1);
-  k_nbr_long_fill<<<unsigned(sm_count() * 8), 256, 0, s>>>(v, longq, nlong, ovf_off, ovf);
+  k_nbr_long_fill<<<unsigned(sm_count() * 8), 256, 0, s>>>(v, cy, longq, nlong, ovf_off, ovf);
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_precond(View v, float* tau, float* sigma, const uint32_t* heavy, int n_heavy,
-                           cudaStream_t s) {
+cudaError_t launch_precond(View v, Carry cy, float* tau, float* sigma, const uint32_t* heavy,
+                           int n_heavy, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
-  k_precond<<<blocks_for(v.n, 256) + n_heavy, 256, 0, s>>>(v, tau, sigma, heavy, n_heavy);
+  k_precond<<<blocks_for(v.n, 256) + n_heavy, 256, 0, s>>>(v, cy, tau, sigma, heavy, n_heavy);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1293,13 +1451,13 @@ cudaError_t launch_mark(View v, const float* u, const uint64_t* cls_scan, double
 
 cudaError_t launch_emit(View v, const float* u, const float* p, const uint64_t* out_off,
                         const int8_t* join_level, uint64_t* nkey, uint8_t* nlevel, float* nu,
-                        float* nubar, float* np_, int64_t nstride, int32_t* src, uint32_t* big,
-                        unsigned long long* nbig, cudaStream_t s) {
+                        float* nubar, float* np_, int64_t nstride, int32_t* src, int32_t* fwd,
+                        uint32_t* big, unsigned long long* nbig, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(nbig, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   k_emit<<<blocks_for(v.n, 256), 256, 0, s>>>(v, u, p, out_off, join_level, nkey, nlevel, nu, nubar,
-                                              np_, nstride, src, big, nbig);
+                                              np_, nstride, src, fwd, big, nbig);
   count_launches(1);
   k_emit_big<<<unsigned(sm_count() * 2), 256, 0, s>>>(v, u, p, out_off, join_level, nkey, nlevel,
                                                       nu, nubar, np_, nstride, src, big, nbig);

@@ -143,6 +143,8 @@ struct Leaves {
   float* sigma = nullptr;
   int32_t* nbr = nullptr;  // [6][cap]
   uint32_t* soff = nullptr;  // [cap + 1]
+  int32_t* ovf = nullptr;  // finer-neighbour lists of nbr
+  int64_t ovf_cap = 0;
 };
 
 // Raw view of the current structure handed to kernels.
@@ -155,6 +157,23 @@ struct View {
   const int32_t* ovf;
   int64_t stride;      // leaf capacity (row pitch of nbr and p)
   const uint32_t* map; // finest voxel (Morton order) -> index of its leaf
+};
+
+// The structure before a split/join pass, handed to the neighbour build of
+// the new one: a kept leaf (same key, same level) whose neighbours across a
+// face were all kept has the same neighbours afterwards, so its entry is
+// carried over with the indices renumbered instead of being searched again.
+// Kept leaves keep their relative order, so carried lists stay ascending.
+struct Carry {
+  const int32_t* nbr = nullptr;  // old [6][stride]; nullptr: build from scratch
+  const int32_t* ovf = nullptr;  // old lists
+  int64_t stride = 0;
+  const int32_t* src = nullptr;  // new leaf -> old index if kept, else -1
+  const int32_t* fwd = nullptr;  // old leaf -> new index if kept, else -1
+  uint32_t* aux = nullptr;       // [6 n]: old list start of a carried list
+  uint8_t* full = nullptr;       // [6 n]: the face was carried
+  const float* tau = nullptr;    // old step sizes (copied for fully carried leaves)
+  const float* sigma = nullptr;
 };
 
 }  // namespace ofu
@@ -200,10 +219,6 @@ struct ofu_ctx {
   void* samp[2] = {nullptr, nullptr};
   int64_t samp_cap[2] = {0, 0};
   int64_t n_samples = 0;
-
-  // overflow lists of finer face neighbours
-  int32_t* ovf = nullptr;
-  int64_t ovf_cap = 0;
 
   // finest voxel -> leaf index of the current structure (8^D entries)
   uint32_t* map = nullptr;
@@ -279,13 +294,13 @@ cudaError_t launch_heavy(View v, const uint32_t* ovf_count, uint64_t* flags, uin
 
 // Face neighbours: count pass (long lists queued in longq and counted by a
 // block each), then the fill.
-cudaError_t launch_nbr_count(View v, int32_t* nbr, uint32_t* ovf_count, uint32_t* longq,
+cudaError_t launch_nbr_count(View v, Carry cy, int32_t* nbr, uint32_t* ovf_count, uint32_t* longq,
                              unsigned long long* nlong, cudaStream_t s);
-cudaError_t launch_nbr_fill(View v, const uint32_t* ovf_off, int32_t* nbr, int32_t* ovf,
+cudaError_t launch_nbr_fill(View v, Carry cy, const uint32_t* ovf_off, int32_t* nbr, int32_t* ovf,
                             const uint32_t* longq, const unsigned long long* nlong,
                             cudaStream_t s);
-cudaError_t launch_precond(View v, float* tau, float* sigma, const uint32_t* heavy, int n_heavy,
-                           cudaStream_t s);
+cudaError_t launch_precond(View v, Carry cy, float* tau, float* sigma, const uint32_t* heavy,
+                           int n_heavy, cudaStream_t s);
 cudaError_t launch_check_tiling(const uint64_t* key, const uint8_t* level, int64_t n, int D,
                                 uint32_t* bad, cudaStream_t s);
 
@@ -297,8 +312,8 @@ cudaError_t launch_mark(View v, const float* u, const uint64_t* cls_scan, double
                         unsigned long long* counters, cudaStream_t s);
 cudaError_t launch_emit(View v, const float* u, const float* p, const uint64_t* out_off,
                         const int8_t* join_level, uint64_t* nkey, uint8_t* nlevel, float* nu,
-                        float* nubar, float* np_, int64_t nstride, int32_t* src, uint32_t* big,
-                        unsigned long long* nbig, cudaStream_t s);
+                        float* nubar, float* np_, int64_t nstride, int32_t* src, int32_t* fwd,
+                        uint32_t* big, unsigned long long* nbig, cudaStream_t s);
 // Voxel -> leaf map of a structure (big: scratch of n entries, nbig: counter).
 cudaError_t launch_map(const uint64_t* key, const uint8_t* level, int64_t n, int D, uint32_t* map,
                        uint32_t* big, unsigned long long* nbig, cudaStream_t s);
