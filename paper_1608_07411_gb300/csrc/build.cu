@@ -1179,12 +1179,33 @@ __global__ void k_copy_kept(const int32_t* __restrict__ src, int64_t n,
     const int32_t sj = j < n ? src[j] : -1;
     const int32_t s0 = __shfl_sync(kFull, sj, 0);
     const bool run = __all_sync(kFull, j < n && s0 >= 0 && sj == s0 + lane);
+    // four loads in flight before their stores (a store waits for its load)
     if (run) {
       const uint32_t a = old_soff[s0], c = old_soff[s0 + 32] - a, b = new_soff[j0];
-      for (uint32_t k = lane; k < c; k += 32) new_samp[b + k] = old_samp[a + k];
+      for (uint32_t k0 = lane; k0 < c; k0 += 128) {
+        T x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t k = k0 + 32u * q;
+          if (k < c) x[q] = old_samp[a + k];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t k = k0 + 32u * q;
+          if (k < c) new_samp[b + k] = x[q];
+        }
+      }
     } else if (sj >= 0) {
       const uint32_t a = old_soff[sj], c = old_soff[sj + 1] - a, b = new_soff[j];
-      for (uint32_t k = 0; k < c; ++k) new_samp[b + k] = old_samp[a + k];
+      for (uint32_t k0 = 0; k0 < c; k0 += 4) {
+        T x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (k0 + q < c) x[q] = old_samp[a + k0 + q];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (k0 + q < c) new_samp[b + k0 + q] = x[q];
+      }
     }
   }
 }

@@ -120,7 +120,10 @@ __device__ __forceinline__ bool eq1_sample(const Cam& k, const float* __restrict
   const float dist = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)));
   const float phi = __fsub_rn(rng, dist);
   if (!(phi >= -eta)) return false;
-  *f = fminf(fmaxf(__fdiv_rn(phi, delta), -1.0f), 1.0f);
+  // Outside the band |phi| < delta the rounded quotient is already beyond
+  // +-1 (rounding is monotone and 1 is exact), so the clamp decides alone.
+  *f = phi >= delta ? 1.0f
+                    : (phi <= -delta ? -1.0f : fminf(fmaxf(__fdiv_rn(phi, delta), -1.0f), 1.0f));
   return true;
 }
 
