@@ -87,6 +87,27 @@ void ofu_default_params(ofu_params* p);
  * released by ofu_destroy.  EINVAL for out-of-range parameters. */
 ofu_status ofu_create_octree(const ofu_params* params, void* cuda_stream, ofu_ctx** out);
 
+/* Device allocator supplied by the caller (for example a framework's caching
+ * allocator).  alloc returns `bytes` of device memory on the current device,
+ * or NULL on failure; free_fn gives back a block that alloc returned, with its
+ * size.  The library may give a block back while work it enqueued earlier on
+ * the context's stream still uses it, and may use a new block from work
+ * enqueued on that stream right away: the allocator must order reuse after
+ * the stream's pending work (a stream-ordered allocator bound to that stream,
+ * as PyTorch's caching allocator is, or one that synchronises). */
+typedef void* (*ofu_alloc_fn)(size_t bytes, void* user);
+typedef void (*ofu_free_fn)(void* ptr, size_t bytes, void* user);
+
+/* ofu_create_octree with every device buffer of the context (leaves, samples,
+ * neighbour lists, voxel map, frames, scratch) taken from alloc and given back
+ * through free_fn; pinned host staging is the library's own.  Both callbacks
+ * must be given (EINVAL otherwise); `user` is passed through.  A NULL from
+ * alloc fails the call that needed the memory with ENOMEM and poisons the
+ * context (only ofu_destroy is valid after it).  ofu_destroy gives back every
+ * block still held, after synchronising the stream. */
+ofu_status ofu_create_octree_ex(const ofu_params* params, void* cuda_stream, ofu_alloc_fn alloc,
+                                ofu_free_fn free_fn, void* user, ofu_ctx** out);
+
 /* Releases everything the context owns.  NULL is ignored. */
 void ofu_destroy(ofu_ctx* ctx);
 

@@ -63,50 +63,77 @@ ofu_status fail_cuda(ofu_ctx* c, cudaError_t e, const char* what) {
     if (s_ != OFU_OK) return s_;                \
   } while (0)
 
+// Device memory of a context: the caller's allocator when one was given,
+// else cudaMalloc / cudaFree.  Live blocks are recorded with their sizes.
+template <typename T>
+cudaError_t dalloc(ofu_ctx* ctx, T** p, size_t bytes) {
+  void* q = nullptr;
+  if (ctx->alloc_fn) {
+    q = ctx->alloc_fn(bytes, ctx->alloc_user);
+    if (!q) return cudaErrorMemoryAllocation;
+  } else {
+    const cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return e;
+  }
+  ctx->live[q] = bytes;
+  *p = static_cast<T*>(q);
+  return cudaSuccess;
+}
+
+cudaError_t dfree(ofu_ctx* ctx, void* p) {
+  if (!p) return cudaSuccess;
+  size_t bytes = 0;
+  const auto it = ctx->live.find(p);
+  if (it != ctx->live.end()) {
+    bytes = it->second;
+    ctx->live.erase(it);
+  }
+  if (ctx->free_fn) {
+    ctx->free_fn(p, bytes, ctx->alloc_user);
+    return cudaSuccess;
+  }
+  return cudaFree(p);
+}
+
 template <typename T>
 ofu_status ensure(ofu_ctx* ctx, Buf b, size_t count, T** out) {
   Bufs& B = bufs(ctx);
   const size_t need = std::max<size_t>(count * sizeof(T), 256);
   if (B.bytes[b] < need) {
-    if (B.p[b]) CU(cudaFree(B.p[b]));
+    if (B.p[b]) CU(dfree(ctx, B.p[b]));
     B.p[b] = nullptr;
     B.bytes[b] = 0;
     const size_t nb = need + need / 4;
-    CU(cudaMalloc(&B.p[b], nb));
+    CU(dalloc(ctx, &B.p[b], nb));
     B.bytes[b] = nb;
   }
   *out = reinterpret_cast<T*>(B.p[b]);
   return OFU_OK;
 }
 
-void free_leaves(Leaves& L) {
-  cudaFree(L.key);
-  cudaFree(L.level);
-  cudaFree(L.u);
-  cudaFree(L.ubar);
-  cudaFree(L.p);
-  cudaFree(L.tau);
-  cudaFree(L.sigma);
-  cudaFree(L.nbr);
-  cudaFree(L.soff);
-  cudaFree(L.ovf);
+void free_leaves(ofu_ctx* ctx, Leaves& L) {
+  for (void* q : {static_cast<void*>(L.key), static_cast<void*>(L.level), static_cast<void*>(L.u),
+                  static_cast<void*>(L.ubar), static_cast<void*>(L.p), static_cast<void*>(L.tau),
+                  static_cast<void*>(L.sigma), static_cast<void*>(L.nbr),
+                  static_cast<void*>(L.soff), static_cast<void*>(L.ovf)})
+    dfree(ctx, q);
   L = Leaves{};
 }
 
 ofu_status ensure_leaves(ofu_ctx* ctx, int which, int64_t need) {
   Leaves& L = ctx->L[which];
   if (L.cap >= need) return OFU_OK;
-  free_leaves(L);
+  free_leaves(ctx, L);
   const int64_t cap = std::max<int64_t>(need + need / 4, 1024);
-  CU(cudaMalloc(&L.key, cap * sizeof(uint64_t)));
-  CU(cudaMalloc(&L.level, cap));
-  CU(cudaMalloc(&L.u, cap * sizeof(float)));
-  CU(cudaMalloc(&L.ubar, cap * sizeof(float)));
-  CU(cudaMalloc(&L.p, 3 * cap * sizeof(float)));
-  CU(cudaMalloc(&L.tau, cap * sizeof(float)));
-  CU(cudaMalloc(&L.sigma, cap * sizeof(float)));
-  CU(cudaMalloc(&L.nbr, 6 * cap * sizeof(int32_t)));
-  CU(cudaMalloc(&L.soff, (cap + 1) * sizeof(uint32_t)));
+  CU(dalloc(ctx, &L.key, cap * sizeof(uint64_t)));
+  CU(dalloc(ctx, &L.level, cap));
+  CU(dalloc(ctx, &L.u, cap * sizeof(float)));
+  CU(dalloc(ctx, &L.ubar, cap * sizeof(float)));
+  CU(dalloc(ctx, &L.p, 3 * cap * sizeof(float)));
+  CU(dalloc(ctx, &L.tau, cap * sizeof(float)));
+  CU(dalloc(ctx, &L.sigma, cap * sizeof(float)));
+  CU(dalloc(ctx, &L.nbr, 6 * cap * sizeof(int32_t)));
+  CU(dalloc(ctx, &L.soff, (cap + 1) * sizeof(uint32_t)));
   L.cap = cap;
   return OFU_OK;
 }
@@ -115,10 +142,10 @@ size_t sample_bytes(const ofu_ctx* ctx) { return ctx->prm.sample_fp16 ? 2 : 4; }
 
 ofu_status ensure_samples(ofu_ctx* ctx, int which, int64_t need) {
   if (ctx->samp_cap[which] >= need && ctx->samp[which]) return OFU_OK;
-  if (ctx->samp[which]) CU(cudaFree(ctx->samp[which]));
+  if (ctx->samp[which]) CU(dfree(ctx, ctx->samp[which]));
   ctx->samp[which] = nullptr;
   const int64_t cap = std::max<int64_t>(need + need / 4, 4096);
-  CU(cudaMalloc(&ctx->samp[which], size_t(cap) * sample_bytes(ctx) + 16));
+  CU(dalloc(ctx, &ctx->samp[which], size_t(cap) * sample_bytes(ctx) + 16));
   ctx->samp_cap[which] = cap;
   return OFU_OK;
 }
@@ -165,7 +192,7 @@ int64_t max_leaves(const ofu_ctx* ctx) {
 // Voxel -> leaf map of the current structure.
 ofu_status rebuild_map(ofu_ctx* ctx) {
   const int D = ctx->prm.max_depth;
-  if (!ctx->map) CU(cudaMalloc(&ctx->map, (size_t(1) << (3 * D)) * sizeof(uint32_t)));
+  if (!ctx->map) CU(dalloc(ctx, &ctx->map, (size_t(1) << (3 * D)) * sizeof(uint32_t)));
   uint32_t* big;
   uint64_t* small;
   ST(ensure(ctx, B_BIG, size_t(ctx->n), &big));
@@ -194,11 +221,11 @@ ofu_status rebuild_topology(ofu_ctx* ctx, const uint32_t* samples_total = nullpt
   ST(ensure(ctx, B_LONGQ, size_t(6 * n), &longq));
   ST(ensure(ctx, B_SMALL, 16, &small));
   if (ctx->heavy_cap < n) {
-    if (ctx->heavy) CU(cudaFree(ctx->heavy));
+    if (ctx->heavy) CU(dfree(ctx, ctx->heavy));
     ctx->heavy = nullptr;
     ctx->heavy_cap = 0;
     const int64_t cap = std::max<int64_t>(n + n / 4, 1024);
-    CU(cudaMalloc(&ctx->heavy, 2 * size_t(cap) * sizeof(uint32_t)));
+    CU(dalloc(ctx, &ctx->heavy, 2 * size_t(cap) * sizeof(uint32_t)));
     ctx->heavy_cap = cap;
   }
   unsigned long long* nlong = reinterpret_cast<unsigned long long*>(small + 8);
@@ -228,12 +255,12 @@ ofu_status rebuild_topology(ofu_ctx* ctx, const uint32_t* samples_total = nullpt
   const uint32_t total = uint32_t(hs[1] & 0xffffffffu);
   if (samples_total) ctx->n_samples = int64_t(hs[1] >> 32);
   if (int64_t(total) + 1 > L.ovf_cap) {
-    if (L.ovf) CU(cudaFree(L.ovf));
+    if (L.ovf) CU(dfree(ctx, L.ovf));
     L.ovf = nullptr;
     L.ovf_cap = 0;
     const int64_t cap = std::max<int64_t>(int64_t(total) + int64_t(total) / 4 + 1, 1024);
     if (cap >= 0x7fffffffLL) return fail(ctx, OFU_ECAPACITY, "neighbour lists exceed 2^31 entries");
-    CU(cudaMalloc(&L.ovf, size_t(cap) * sizeof(int32_t)));
+    CU(dalloc(ctx, &L.ovf, size_t(cap) * sizeof(int32_t)));
     L.ovf_cap = cap;
   }
   v = view_of(ctx);
@@ -321,8 +348,18 @@ void ofu_default_params(ofu_params* p) {
 }
 
 ofu_status ofu_create_octree(const ofu_params* params, void* cuda_stream, ofu_ctx** out) {
+  return ofu_create_octree_ex(params, cuda_stream, nullptr, nullptr, nullptr, out);
+}
+
+ofu_status ofu_create_octree_ex(const ofu_params* params, void* cuda_stream, ofu_alloc_fn alloc,
+                                ofu_free_fn free_fn, void* user, ofu_ctx** out) {
   if (!out) {
     g_create_error = "out is NULL";
+    return OFU_EINVAL;
+  }
+  if ((alloc == nullptr) != (free_fn == nullptr)) {
+    *out = nullptr;
+    g_create_error = "create_octree_ex: give both alloc and free_fn, or neither";
     return OFU_EINVAL;
   }
   *out = nullptr;
@@ -334,6 +371,9 @@ ofu_status ofu_create_octree(const ofu_params* params, void* cuda_stream, ofu_ct
   ofu_ctx* ctx = new ofu_ctx();
   ctx->prm = *params;
   ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  ctx->alloc_fn = alloc;
+  ctx->free_fn = free_fn;
+  ctx->alloc_user = user;
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = cudaMallocHost(&ctx->pinned, 256);
   if (e != cudaSuccess) {
@@ -350,17 +390,17 @@ ofu_status ofu_create_octree(const ofu_params* params, void* cuda_stream, ofu_ct
 void ofu_destroy(ofu_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
-  free_leaves(ctx->L[0]);
-  free_leaves(ctx->L[1]);
-  cudaFree(ctx->samp[0]);
-  cudaFree(ctx->samp[1]);
-  cudaFree(ctx->depth);
-  cudaFree(ctx->cams);
-  cudaFree(ctx->map);
-  cudaFree(ctx->heavy);
+  free_leaves(ctx, ctx->L[0]);
+  free_leaves(ctx, ctx->L[1]);
+  dfree(ctx, ctx->samp[0]);
+  dfree(ctx, ctx->samp[1]);
+  dfree(ctx, ctx->depth);
+  dfree(ctx, ctx->cams);
+  dfree(ctx, ctx->map);
+  dfree(ctx, ctx->heavy);
   if (ctx->scratch) {
     Bufs& B = bufs(ctx);
-    for (int b = 0; b < B_NUM; ++b) cudaFree(B.p[b]);
+    for (int b = 0; b < B_NUM; ++b) dfree(ctx, B.p[b]);
     delete &B;
   }
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
@@ -403,13 +443,13 @@ ofu_status ofu_integrate_frames(ofu_ctx* ctx, int32_t F, int32_t H, int32_t W, c
   }
   const size_t dbytes = size_t(F) * H * W * sizeof(float);
   if (ctx->depth && size_t(ctx->F) * ctx->H * ctx->W * sizeof(float) < dbytes) {
-    CU(cudaFree(ctx->depth));
+    CU(dfree(ctx, ctx->depth));
     ctx->depth = nullptr;
   }
-  if (!ctx->depth) CU(cudaMalloc(&ctx->depth, dbytes));
-  if (ctx->cams) CU(cudaFree(ctx->cams));
+  if (!ctx->depth) CU(dalloc(ctx, &ctx->depth, dbytes));
+  if (ctx->cams) CU(dfree(ctx, ctx->cams));
   ctx->cams = nullptr;
-  CU(cudaMalloc(&ctx->cams, size_t(F) * sizeof(Cam)));
+  CU(dalloc(ctx, &ctx->cams, size_t(F) * sizeof(Cam)));
   CU(cudaMemcpyAsync(ctx->depth, depth, dbytes, cudaMemcpyDefault, ctx->stream));
   CU(cudaMemcpyAsync(ctx->cams, cams.data(), size_t(F) * sizeof(Cam), cudaMemcpyHostToDevice, ctx->stream));
   CU(launch_range_map(ctx->depth, ctx->cams, F, H, W, ctx->stream));
@@ -1058,14 +1098,14 @@ ofu_status ofu_load(ofu_ctx* ctx, const char* path) {
   // frames (range maps) and parameters, then the structure and the iterate
   ctx->prm = prm;
   const size_t fr = rmap.size();
-  if (ctx->depth) CU(cudaFree(ctx->depth));
-  if (ctx->cams) CU(cudaFree(ctx->cams));
-  if (ctx->map) CU(cudaFree(ctx->map));
+  if (ctx->depth) CU(dfree(ctx, ctx->depth));
+  if (ctx->cams) CU(dfree(ctx, ctx->cams));
+  if (ctx->map) CU(dfree(ctx, ctx->map));
   ctx->depth = nullptr;
   ctx->cams = nullptr;
   ctx->map = nullptr;
-  CU(cudaMalloc(&ctx->depth, fr * 4));
-  CU(cudaMalloc(&ctx->cams, cams.size() * sizeof(Cam)));
+  CU(dalloc(ctx, &ctx->depth, fr * 4));
+  CU(dalloc(ctx, &ctx->cams, cams.size() * sizeof(Cam)));
   CU(cudaMemcpy(ctx->depth, rmap.data(), fr * 4, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(ctx->cams, cams.data(), cams.size() * sizeof(Cam), cudaMemcpyHostToDevice));
   ctx->F = dims[0];

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/octfuse.h"
@@ -204,6 +205,13 @@ struct ofu_ctx {
   ofu_params prm{};
   cudaStream_t stream = nullptr;
   int device = 0;
+
+  // device memory: the caller's allocator (ofu_create_octree_ex) or cudaMalloc;
+  // live blocks with their sizes (the free callback is given the size)
+  ofu_alloc_fn alloc_fn = nullptr;
+  ofu_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
+  std::unordered_map<void*, size_t> live;
   std::string err;
   bool poisoned = false;
 

@@ -53,9 +53,15 @@ _P64 = ctypes.POINTER(ctypes.c_int64)
 _PD = ctypes.POINTER(ctypes.c_double)
 _PI32 = ctypes.POINTER(ctypes.c_int32)
 
+# device allocator callbacks of ofu_create_octree_ex
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
 _SIGS = {
     "ofu_default_params": (None, [ctypes.POINTER(Params)]),
     "ofu_create_octree": (_i32, [ctypes.POINTER(Params), _vp, ctypes.POINTER(_vp)]),
+    "ofu_create_octree_ex": (_i32, [ctypes.POINTER(Params), _vp, ALLOC_FN, FREE_FN, _vp,
+                                    ctypes.POINTER(_vp)]),
     "ofu_destroy": (None, [_vp]),
     "ofu_last_error": (ctypes.c_char_p, [_vp]),
     "ofu_integrate_frames": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _vp]),
@@ -149,8 +155,27 @@ def ofu_create_octree(params: Params, stream: int = 0) -> int:
     return out.value
 
 
+# callback objects of live contexts (ctypes frees a callback's trampoline
+# when its Python object dies, so each is kept until ofu_destroy)
+_allocators = {}
+
+
+def ofu_create_octree_ex(params: Params, stream: int, alloc, free) -> int:
+    """Context whose device memory comes from alloc(nbytes) -> int pointer (0 on
+    failure) and goes back through free(ptr, nbytes)."""
+    a = ALLOC_FN(lambda nbytes, user: alloc(nbytes) or None)
+    f = FREE_FN(lambda ptr, nbytes, user: free(ptr, nbytes))
+    out = _vp()
+    st = load().ofu_create_octree_ex(ctypes.byref(params), _vp(stream or None), a, f, None,
+                                     ctypes.byref(out))
+    _check(None, st)
+    _allocators[out.value] = (a, f)
+    return out.value
+
+
 def ofu_destroy(ctx: int) -> None:
     load().ofu_destroy(ctx)
+    _allocators.pop(ctx, None)
 
 
 def ofu_last_error(ctx: int = 0) -> str:
@@ -337,8 +362,12 @@ def params_for(scene, sample_fp16: bool = False, max_leaves: int = 0) -> Params:
 class Octree:
     """Owns one context; methods mirror the C ABI with NumPy host buffers."""
 
-    def __init__(self, params: Params, stream: int = 0):
-        self.ctx = ofu_create_octree(params, stream)
+    def __init__(self, params: Params, stream: int = 0, allocator=None):
+        """allocator: optional (alloc, free) pair for ofu_create_octree_ex."""
+        if allocator is None:
+            self.ctx = ofu_create_octree(params, stream)
+        else:
+            self.ctx = ofu_create_octree_ex(params, stream, *allocator)
 
     def close(self):
         if self.ctx:

@@ -78,3 +78,13 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(octfuse, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         octfuse.load(str(tmp_path / "nope.so"))
+
+
+def test_allocator_callbacks_come_in_pairs(lib):
+    p = octfuse.ofu_default_params()
+    out = ctypes.c_void_p()
+    alloc = octfuse.ALLOC_FN(lambda n, user: None)
+    st = lib.ofu_create_octree_ex(ctypes.byref(p), None, alloc, octfuse.FREE_FN(), None,
+                                  ctypes.byref(out))
+    assert st == octfuse.OFU_EINVAL and out.value is None
+    assert "both" in octfuse.ofu_last_error()
