@@ -327,9 +327,16 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     s0s = []
+    cons_ev = []
 
-    def step():
+    def step(timed=False):
+        if timed:
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
         of.ofu_integrate_frames(ctx, F, H, W, depth_d.data_ptr(), intr_d.data_ptr(), pose_d.data_ptr())
+        if timed:
+            c1.record(stream)
+            cons_ev.append((c0, c1))
         n0 = of.ofu_num_leaves(ctx)
         s0s.append(of.ofu_export_field(ctx, of.FIELD_SAMPLES, None, 0))
         done, li, e = of.ofu_solve(ctx, iters, R, 0, 0.0)
@@ -355,7 +362,7 @@ def main():
         flush.zero_()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        n0, li, energies = step()
+        n0, li, energies = step(timed=True)
         ev1.record(stream)
         ev1.synchronize()
         times.append(ev0.elapsed_time(ev1))
@@ -411,6 +418,16 @@ def main():
                       if ms[1 - dom] > 0 else 0.0, "avg_launch_us": 1e3 * ms[1 - dom] / max(nl[1 - dom], 1)},
             "iteration_share_of_step": (ms[0] + ms[1]) / sum(times)}
 
+    # iteration kernels alone, and the construction (Eq. 1 at every finest voxel for the
+    # median field, then count and fill passes over the leaves) on its own
+    iterate_only = {"value": leaf_iters / ((ms[0] + ms[1]) * 1e-3) if ms[0] + ms[1] > 0 else 0.0,
+                    "unit": METRIC, "kernels": list(names), "scope": "rank 0"}
+    cons_ms = statistics.median(c0.elapsed_time(c1) for c0, c1 in cons_ev)
+    evals = (8 ** scene.max_depth + 2 * int(statistics.median(n0s))) * F
+    construction = {"ms": cons_ms, "eq1_evaluations": evals,
+                    "eq1_evaluations_per_s": evals / (cons_ms * 1e-3), "finest_voxels": 8 ** scene.max_depth,
+                    "frames": F, "share_of_step": cons_ms * a.steps / sum(times)}
+
     tte = None if a.no_tte else time_to_energy(a, scene, of, stream, depth_d, intr_d, pose_d)
 
     cpu = None
@@ -434,6 +451,7 @@ def main():
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
             "roofline": roof, "clocks": clk, "cpu_baseline": cpu, "time_to_energy": tte,
+            "iterate_only": iterate_only, "construction": construction,
         }
         print(json.dumps(line), flush=True)
     of.ofu_destroy(ctx)
