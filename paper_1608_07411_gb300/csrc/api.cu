@@ -469,7 +469,12 @@ ofu_status ofu_integrate_frames(ofu_ctx* ctx, int32_t F, int32_t H, int32_t W, c
   ST(ensure(ctx, B_FLAGS, size_t(nvox), &flags));
   ST(ensure(ctx, B_POS, size_t(nvox + 1), &pos));
   ST(ensure(ctx, B_SCAN, scan_tmp_items<uint32_t>(nvox) * 2, &tmp));
-  CU(launch_dense_u0(ctx->depth, ctx->cams, F, H, W, g, u0, ctx->stream));
+  uint64_t* small;
+  ST(ensure(ctx, B_SMALL, 16, &small));
+  // pos is free until the leaf flags are scanned: it holds the voxels whose
+  // median needs a sort
+  CU(launch_dense_u0(ctx->depth, ctx->cams, F, H, W, g, u0, pos,
+                     reinterpret_cast<unsigned long long*>(small + 12), ctx->stream));
   CU(launch_pyramid(u0, D, pyr, pyr + npyr, ctx->stream));
   CU(launch_leaf_flags(pyr, pyr + npyr, D, ctx->prm.spread_tau, flags, ctx->stream));
   CU(scan_exclusive<uint32_t>(flags, pos, nvox, tmp, ctx->stream));

@@ -218,10 +218,61 @@ __device__ __forceinline__ int warp_samples(const Cam* sc, const float* depth, i
   return warp_sum_i(cnt);
 }
 
+// Median field, first pass: a thread per finest voxel walks all frames and
+// keeps W, min and max of the observed Eq. 1 samples.  The median is final
+// where W = 0 (-1) or every observed sample is the same value; the other
+// voxels (near a surface) are queued for the warp sort of k_dense_u0.
+// Warps stride over the voxels together, so every lane reaches the ballot.
+__global__ void __launch_bounds__(256) k_dense_scan(const float* __restrict__ depth,
+                                                    const Cam* __restrict__ cams, int F, int H,
+                                                    int W, Geo g, int64_t nvox,
+                                                    double* __restrict__ u0,
+                                                    uint32_t* __restrict__ queue,
+                                                    unsigned long long* __restrict__ nqueue) {
+  extern __shared__ float4 smem_dyn[];
+  Cam* sc = reinterpret_cast<Cam*>(smem_dyn);
+  stage_cams(sc, cams, F);
+  const int lane = lane_id();
+  for (int64_t m0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) & ~int64_t(31); m0 < nvox;
+       m0 += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t m = m0 + lane;
+    bool sort = false;
+    if (m < nvox) {
+      const uint32_t ix = compact3(uint64_t(m)), iy = compact3(uint64_t(m) >> 1),
+                     iz = compact3(uint64_t(m) >> 2);
+      const float x = centre_coord(g.org[0], ix, 1, g.vox);
+      const float y = centre_coord(g.org[1], iy, 1, g.vox);
+      const float z = centre_coord(g.org[2], iz, 1, g.vox);
+      int cnt = 0;
+      float lo = CUDART_INF_F, hi = -CUDART_INF_F;
+      for (int i = 0; i < F; ++i) {
+        float t;
+        if (eq1_sample(sc[i], depth + size_t(i) * H * W, H, W, x, y, z, g.delta, g.eta, &t)) {
+          ++cnt;
+          lo = fminf(lo, t);
+          hi = fmaxf(hi, t);
+        }
+      }
+      sort = cnt > 0 && lo != hi;
+      if (!sort) u0[m] = cnt == 0 ? -1.0 : double(lo);
+    }
+    const unsigned bal = __ballot_sync(kFull, sort);
+    if (bal) {
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(nqueue, static_cast<unsigned long long>(__popc(bal)));
+      base = __shfl_sync(kFull, base, 0);
+      if (sort) queue[base + __popc(bal & ((1u << lane) - 1))] = uint32_t(m);
+    }
+  }
+}
+
+// Median field, second pass: a warp per queued voxel (one frame per lane)
+// sorts the samples in shared memory and takes the median.
 template <int P>
 __global__ void __launch_bounds__(256) k_dense_u0(const float* __restrict__ depth,
                                                   const Cam* __restrict__ cams, int F, int H,
-                                                  int W, Geo g, int64_t nvox,
+                                                  int W, Geo g, const uint32_t* __restrict__ queue,
+                                                  const unsigned long long* __restrict__ nqueue,
                                                   double* __restrict__ u0) {
   extern __shared__ float4 smem_dyn[];
   Cam* sc = reinterpret_cast<Cam*>(smem_dyn);
@@ -229,8 +280,10 @@ __global__ void __launch_bounds__(256) k_dense_u0(const float* __restrict__ dept
   stage_cams(sc, cams, F);
   const int warp = threadIdx.x >> 5;
   float* a = bufs + warp * P;
-  for (int64_t m = int64_t(blockIdx.x) * kWarpsPerBlock + warp; m < nvox;
-       m += int64_t(gridDim.x) * kWarpsPerBlock) {
+  const int64_t nq = int64_t(*nqueue);
+  for (int64_t j = int64_t(blockIdx.x) * kWarpsPerBlock + warp; j < nq;
+       j += int64_t(gridDim.x) * kWarpsPerBlock) {
+    const int64_t m = queue[j];
     const uint32_t ix = compact3(uint64_t(m)), iy = compact3(uint64_t(m) >> 1),
                    iz = compact3(uint64_t(m) >> 2);
     const float x = centre_coord(g.org[0], ix, 1, g.vox);
@@ -1291,23 +1344,34 @@ template cudaError_t scan_exclusive<uint64_t>(const uint64_t*, uint64_t*, int64_
 
 template <int P>
 static cudaError_t dense_u0_p(const float* depth, const Cam* cams, int F, int H, int W, Geo g,
-                              double* u0, cudaStream_t s) {
+                              double* u0, uint32_t* queue, unsigned long long* nqueue,
+                              cudaStream_t s) {
   const int64_t nvox = int64_t(1) << (3 * g.D);
-  const size_t sm = size_t(F) * sizeof(Cam) + size_t(kWarpsPerBlock) * P * sizeof(float);
+  cudaError_t e = cudaMemsetAsync(nqueue, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const size_t sm0 = size_t(F) * sizeof(Cam);
+  if (sm0 > 48 * 1024) cudaFuncSetAttribute(k_dense_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm0));
+  const int64_t want = (nvox + 255) / 256, cap = int64_t(sm_count()) * 16;
+  k_dense_scan<<<unsigned(want < cap ? want : cap), 256, sm0, s>>>(depth, cams, F, H, W, g, nvox, u0,
+                                                                 queue, nqueue);
+  count_launches(1);
+  const size_t sm = sm0 + size_t(kWarpsPerBlock) * P * sizeof(float);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_dense_u0<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-  k_dense_u0<P><<<warp_grid(nvox), 32 * kWarpsPerBlock, sm, s>>>(depth, cams, F, H, W, g, nvox, u0);
+  k_dense_u0<P><<<warp_grid(nvox), 32 * kWarpsPerBlock, sm, s>>>(depth, cams, F, H, W, g, queue,
+                                                                 nqueue, u0);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dense_u0(const float* depth, const Cam* cams, int F, int H, int W, Geo g,
-                            double* u0, cudaStream_t s) {
+                            double* u0, uint32_t* queue, unsigned long long* nqueue,
+                            cudaStream_t s) {
   switch (pad_frames(F)) {
-    case 32: return dense_u0_p<32>(depth, cams, F, H, W, g, u0, s);
-    case 64: return dense_u0_p<64>(depth, cams, F, H, W, g, u0, s);
-    case 128: return dense_u0_p<128>(depth, cams, F, H, W, g, u0, s);
-    case 256: return dense_u0_p<256>(depth, cams, F, H, W, g, u0, s);
-    case 512: return dense_u0_p<512>(depth, cams, F, H, W, g, u0, s);
+    case 32: return dense_u0_p<32>(depth, cams, F, H, W, g, u0, queue, nqueue, s);
+    case 64: return dense_u0_p<64>(depth, cams, F, H, W, g, u0, queue, nqueue, s);
+    case 128: return dense_u0_p<128>(depth, cams, F, H, W, g, u0, queue, nqueue, s);
+    case 256: return dense_u0_p<256>(depth, cams, F, H, W, g, u0, queue, nqueue, s);
+    case 512: return dense_u0_p<512>(depth, cams, F, H, W, g, u0, queue, nqueue, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -272,9 +272,11 @@ cudaError_t scan_exclusive(const T* in, T* out, int64_t n, T* tmp, cudaStream_t 
 cudaError_t launch_range_map(float* depth, const Cam* cams, int F, int H, int W, cudaStream_t s);
 
 // Median field at finest-voxel centres (Morton order), then the Eq. 2 min/max
-// pyramid and the per-voxel leaf flags.
+// pyramid and the per-voxel leaf flags.  launch_dense_u0 needs a queue of
+// 8^D entries and a device counter as scratch.
 cudaError_t launch_dense_u0(const float* depth, const Cam* cams, int F, int H, int W, Geo g,
-                            double* u0, cudaStream_t s);
+                            double* u0, uint32_t* queue, unsigned long long* nqueue,
+                            cudaStream_t s);
 cudaError_t launch_pyramid(const double* u0, int D, double* mn, double* mx, cudaStream_t s);
 cudaError_t launch_leaf_flags(const double* mn, const double* mx, int D, double spread_tau,
                               uint32_t* flags, cudaStream_t s);
