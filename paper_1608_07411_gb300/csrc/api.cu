@@ -26,7 +26,7 @@ thread_local std::string g_create_error;
 // Persistent device buffers by role (content not kept across growth).
 enum Buf {
   B_SCAN, B_U0, B_PYR, B_FLAGS, B_POS, B_CNT, B_OVFC, B_CLS, B_OUTC, B_JL, B_SRC, B_LIST,
-  B_SMALL, B_PART, B_BIG, B_LONGQ, B_FWD, B_AUX, B_FULL, B_NUM
+  B_SMALL, B_PART, B_BIG, B_LONGQ, B_FWD, B_AUX, B_FULL, B_PENDQ, B_NUM
 };
 
 struct Bufs {
@@ -219,6 +219,8 @@ ofu_status rebuild_topology(ofu_ctx* ctx, const uint32_t* samples_total = nullpt
   ST(ensure(ctx, B_OVFC, size_t(6 * n + 1), &ovfc));
   ST(ensure(ctx, B_SCAN, scan_tmp_items<uint32_t>(6 * n) * 2, &tmp));
   ST(ensure(ctx, B_LONGQ, size_t(6 * n), &longq));
+  uint32_t* pendq;
+  ST(ensure(ctx, B_PENDQ, size_t(6 * n), &pendq));
   ST(ensure(ctx, B_SMALL, 16, &small));
   if (ctx->heavy_cap < n) {
     if (ctx->heavy) CU(dfree(ctx, ctx->heavy));
@@ -229,6 +231,7 @@ ofu_status rebuild_topology(ofu_ctx* ctx, const uint32_t* samples_total = nullpt
     ctx->heavy_cap = cap;
   }
   unsigned long long* nlong = reinterpret_cast<unsigned long long*>(small + 8);
+  unsigned long long* npend = reinterpret_cast<unsigned long long*>(small + 11);
   uint64_t *hflags, *htmp;
   ST(ensure(ctx, B_CLS, size_t(n + 1), &hflags));
   ST(ensure(ctx, B_OUTC, scan_tmp_items<uint64_t>(n) * 2, &htmp));
@@ -238,7 +241,7 @@ ofu_status rebuild_topology(ofu_ctx* ctx, const uint32_t* samples_total = nullpt
   }
   Leaves& L = ctx->L[ctx->cur];
   View v = view_of(ctx);
-  CU(launch_nbr_count(v, carry, L.nbr, ovfc, longq, nlong, ctx->stream));
+  CU(launch_nbr_count(v, carry, L.nbr, ovfc, longq, nlong, pendq, npend, ctx->stream));
   CU(launch_heavy(v, ovfc, hflags, htmp, ctx->heavy, ctx->heavy + ctx->heavy_cap, ctx->stream));
   CU(scan_exclusive<uint32_t>(ovfc, ovfc, 6 * n, tmp, ctx->stream));
   // one read-back: packed heavy counts (slot 9), [list total, samples] (slot 10)
@@ -264,7 +267,7 @@ ofu_status rebuild_topology(ofu_ctx* ctx, const uint32_t* samples_total = nullpt
     L.ovf_cap = cap;
   }
   v = view_of(ctx);
-  CU(launch_nbr_fill(v, carry, ovfc, L.nbr, L.ovf, longq, nlong, ctx->stream));
+  CU(launch_nbr_fill(v, carry, ovfc, L.nbr, L.ovf, longq, nlong, pendq, npend, ctx->stream));
   v = view_of(ctx);
   CU(launch_precond(v, carry, L.tau, L.sigma, ctx->heavy + ctx->heavy_cap, ctx->n_heavy_primal,
                     ctx->stream));

@@ -612,16 +612,17 @@ constexpr uint32_t kCarryBit = 0x80000000u;
 constexpr uint32_t kSearch = 0xffffffffu;
 constexpr uint32_t kNotList = 0xfffffffeu;
 
-// One thread per (leaf, face).  Entries carried from the old structure and
-// single neighbours and boundaries are final here; finer lists are counted
-// (small squares and short carried lists by this thread, larger ones queued
-// for a block) and marked pending for the fill pass.  With a carry,
-// cy.full[t] = 1 when the face was carried here.
-__global__ void k_nbr_count(View v, Carry cy, int32_t* __restrict__ nbr,
-                            uint32_t* __restrict__ ovf_count, uint32_t* __restrict__ longq,
-                            unsigned long long* __restrict__ nlong) {
-  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= 6 * v.n) return;
+// Face `face` of leaf l (t = face * n + l): an entry carried from the old
+// structure, a single neighbour or a boundary is final here; a finer list is
+// counted (a small square or a short carried list by this thread, larger ones
+// queued for a block) and marked pending for the fill pass.  With a carry,
+// cy.full[t] = 1 when the face was carried here.  Returns whether the entry
+// is pending.
+__device__ __forceinline__ bool count_face(const View& v, const Carry& cy, int64_t t,
+                                           int32_t* __restrict__ nbr,
+                                           uint32_t* __restrict__ ovf_count,
+                                           uint32_t* __restrict__ longq,
+                                           unsigned long long* __restrict__ nlong) {
   const int face = int(t / v.n);
   const int64_t l = t - int64_t(face) * v.n;
   const int64_t slot = int64_t(face) * v.stride + l;
@@ -649,7 +650,7 @@ __global__ void k_nbr_count(View v, Carry cy, int32_t* __restrict__ nbr,
           ovf_count[t] = 1;  // k_nbr_long_count decides
           longq[atomicAdd(nlong, 1ull)] = uint32_t(t) | kCarryBit;
           cy.full[t] = 0;
-          return;
+          return true;
         }
         bool all = true;
         for (uint32_t k = 0; k < c; ++k) all &= cy.fwd[entry_idx(cy.ovf[so + 1 + k])] >= 0;
@@ -657,12 +658,13 @@ __global__ void k_nbr_count(View v, Carry cy, int32_t* __restrict__ nbr,
           nbr[slot] = kCarryPending;
           cy.aux[t] = so;
           ovf_count[t] = 1 + c;
-          carried = 1;
+          cy.full[t] = 1;
+          return true;
         }
       }
     }
     cy.full[t] = carried;
-    if (carried) return;
+    if (carried) return false;
   }
   const FaceHit f = face_query(v, l, face);
   int32_t e = kEmpty;
@@ -682,42 +684,68 @@ __global__ void k_nbr_count(View v, Carry cy, int32_t* __restrict__ nbr,
   }
   nbr[slot] = e;
   ovf_count[t] = cnt;
+  return f.kind == 2;
 }
 
-// Writes the finer-neighbour lists of small squares and short carried lists
-// (pending entries only; every other thread returns after one load) and
-// points each pending entry at its list.
-__global__ void k_nbr_fill(View v, Carry cy, const uint32_t* __restrict__ ovf_off,
-                           int32_t* __restrict__ nbr, int32_t* __restrict__ ovf) {
+// One thread per (leaf, face) (count_face); the pending slots are appended to
+// pendq, one atomic per warp (every lane reaches the ballot: the grid is whole
+// warps and nothing returns early), so the fill pass visits only them.
+__global__ void k_nbr_count(View v, Carry cy, int32_t* __restrict__ nbr,
+                            uint32_t* __restrict__ ovf_count, uint32_t* __restrict__ longq,
+                            unsigned long long* __restrict__ nlong, uint32_t* __restrict__ pendq,
+                            unsigned long long* __restrict__ npend) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= 6 * v.n) return;
-  const int face = int(t / v.n);
-  const int64_t l = t - int64_t(face) * v.n;
-  const int64_t slot = int64_t(face) * v.stride + l;
-  const int32_t e = nbr[slot];
-  if (e != kListPending && e != kCarryPending) return;
-  const uint32_t st = ovf_off[t];
-  if (e == kCarryPending) {
-    const uint32_t so = cy.aux[t];
-    const int32_t c = cy.ovf[so];
-    for (int32_t k = 0; k < c; ++k) {
-      const int32_t eo = cy.ovf[so + 1 + k];
-      ovf[st + 1 + k] = make_single(uint32_t(cy.fwd[entry_idx(eo)]), entry_level(eo));
-    }
-    ovf[st] = c;
-  } else {
-    const FaceSquare q = face_square(v, l, face);
-    if (q.h * q.h <= kThreadSquare) {
-      uint32_t c = 0;
-#pragma unroll 4
-      for (uint32_t i = 0; i < q.h * q.h; ++i) {
-        const int64_t m = face_rep(v, q, i);
-        if (m >= 0) ovf[st + 1 + c++] = make_single(uint32_t(m), v.level[m]);
-      }
-      ovf[st] = int32_t(c);
-    }
+  const bool pend = t < 6 * v.n && count_face(v, cy, t, nbr, ovf_count, longq, nlong);
+  const unsigned bal = __ballot_sync(kFull, pend);
+  if (bal) {
+    const int lane = lane_id();
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(npend, static_cast<unsigned long long>(__popc(bal)));
+    base = __shfl_sync(kFull, base, 0);
+    if (pend) pendq[base + __popc(bal & ((1u << lane) - 1))] = uint32_t(t);
   }
-  nbr[slot] = make_list(st);
+}
+
+// Pending slots only: writes the finer-neighbour lists of small squares and
+// short carried lists and points each pending entry at its list (a long list
+// gets only its pointer here; a long carry candidate that turned out single
+// is no longer pending and is skipped).
+__global__ void k_nbr_fill(View v, Carry cy, const uint32_t* __restrict__ ovf_off,
+                           int32_t* __restrict__ nbr, int32_t* __restrict__ ovf,
+                           const uint32_t* __restrict__ pendq,
+                           const unsigned long long* __restrict__ npend) {
+  const int64_t np = int64_t(*npend);
+  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < np;
+       j += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t t = pendq[j];
+    const int face = int(t / v.n);
+    const int64_t l = t - int64_t(face) * v.n;
+    const int64_t slot = int64_t(face) * v.stride + l;
+    const int32_t e = nbr[slot];
+    if (e != kListPending && e != kCarryPending) continue;
+    const uint32_t st = ovf_off[t];
+    if (e == kCarryPending) {
+      const uint32_t so = cy.aux[t];
+      const int32_t c = cy.ovf[so];
+      for (int32_t k = 0; k < c; ++k) {
+        const int32_t eo = cy.ovf[so + 1 + k];
+        ovf[st + 1 + k] = make_single(uint32_t(cy.fwd[entry_idx(eo)]), entry_level(eo));
+      }
+      ovf[st] = c;
+    } else {
+      const FaceSquare q = face_square(v, l, face);
+      if (q.h * q.h <= kThreadSquare) {
+        uint32_t c = 0;
+#pragma unroll 4
+        for (uint32_t i = 0; i < q.h * q.h; ++i) {
+          const int64_t m = face_rep(v, q, i);
+          if (m >= 0) ovf[st + 1 + c++] = make_single(uint32_t(m), v.level[m]);
+        }
+        ovf[st] = int32_t(c);
+      }
+    }
+    nbr[slot] = make_list(st);
+  }
 }
 
 // Block-wide ordered walk of a face square: calls emit(position, leaf) for
@@ -1466,11 +1494,14 @@ cudaError_t launch_leaf_fill(const uint64_t* key, const uint8_t* level, const ui
 }
 
 cudaError_t launch_nbr_count(View v, Carry cy, int32_t* nbr, uint32_t* ovf_count, uint32_t* longq,
-                             unsigned long long* nlong, cudaStream_t s) {
+                             unsigned long long* nlong, uint32_t* pendq, unsigned long long* npend,
+                             cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(nlong, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(npend, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k_nbr_count<<<blocks_for(6 * v.n, 256), 256, 0, s>>>(v, cy, nbr, ovf_count, longq, nlong);
+  k_nbr_count<<<blocks_for(6 * v.n, 256), 256, 0, s>>>(v, cy, nbr, ovf_count, longq, nlong, pendq,
+                                                       npend);
   count_launches(1);
   k_nbr_long_count<<<unsigned(sm_count() * 8), 256, 0, s>>>(v, cy, longq, nlong, nbr, ovf_count);
   count_launches(1);
@@ -1479,9 +1510,11 @@ cudaError_t launch_nbr_count(View v, Carry cy, int32_t* nbr, uint32_t* ovf_count
 
 cudaError_t launch_nbr_fill(View v, Carry cy, const uint32_t* ovf_off, int32_t* nbr, int32_t* ovf,
                             const uint32_t* longq, const unsigned long long* nlong,
+                            const uint32_t* pendq, const unsigned long long* npend,
                             cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
-  k_nbr_fill<<<blocks_for(6 * v.n, 256), 256, 0, s>>>(v, cy, ovf_off, nbr, ovf);
+  const int64_t want = blocks_for(6 * v.n, 256), cap = int64_t(sm_count()) * 8;
+  k_nbr_fill<<<unsigned(want < cap ? want : cap), 256, 0, s>>>(v, cy, ovf_off, nbr, ovf, pendq, npend);
   count_launches(1);
   k_nbr_long_fill<<<unsigned(sm_count() * 8), 256, 0, s>>>(v, cy, longq, nlong, ovf_off, ovf);
   count_launches(1);

@@ -308,9 +308,11 @@ cudaError_t launch_heavy(View v, const uint32_t* ovf_count, uint64_t* flags, uin
 // Face neighbours: count pass (long lists queued in longq and counted by a
 // block each), then the fill.
 cudaError_t launch_nbr_count(View v, Carry cy, int32_t* nbr, uint32_t* ovf_count, uint32_t* longq,
-                             unsigned long long* nlong, cudaStream_t s);
+                             unsigned long long* nlong, uint32_t* pendq, unsigned long long* npend,
+                             cudaStream_t s);
 cudaError_t launch_nbr_fill(View v, Carry cy, const uint32_t* ovf_off, int32_t* nbr, int32_t* ovf,
                             const uint32_t* longq, const unsigned long long* nlong,
+                            const uint32_t* pendq, const unsigned long long* npend,
                             cudaStream_t s);
 cudaError_t launch_precond(View v, Carry cy, float* tau, float* sigma, const uint32_t* heavy,
                            int n_heavy, cudaStream_t s);
