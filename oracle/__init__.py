@@ -18,6 +18,9 @@ Modules
   operators  level-aware forward-difference gradient, divergence, step sizes
   solver     normalised TV-L1 energy (Eq. 5), its primal-dual solver, gap
   dense      an independent dense-grid solver (the fully refined special case)
+  mlp        the per-leaf warm-start network (features, forward, gradient, Adam)
+  descent    the paper's own solver: gradient descent on the eps-L1 energy
+             (Eq. 4-6, Sec. 4 schedule); no CUDA counterpart yet
 
 Parity unpinned: nothing in the oracle reproduces the paper's printed results
 (Tables 1-2, the accuracy figures), which need the paper's datasets and its
