@@ -175,6 +175,23 @@ ofu_status ofu_export_leaves(ofu_ctx* ctx, uint64_t* keys, uint8_t* levels, floa
 ofu_status ofu_solve(ofu_ctx* ctx, int32_t iters, int32_t restructure_every, int32_t check_every,
                      double gap_tol, int32_t* iters_done, int64_t* leaf_iters, double* energies3);
 
+/* The paper's own solver (Eq. 4-6; step schedule of Sec. 4): n iterations of
+ * gradient descent on the eps-L1-smoothed normalised energy
+ *   E_eps(u) = sum_l h_l^3 [c_l sum_k G(u_l - f_k) + lambda G(|grad u (l)|)],
+ *   G(x) = sqrt(x^2 + eps^2),  c_l = 1 / (W_l + gamma),
+ * on the current structure, with the same level-aware gradient and divergence
+ * as ofu_iterate.  Iteration t0 + i (0-based) takes the step
+ * xi = xi0 * 0.5^floor((t0 + i) / halve_every) (the paper: xi0 = 0.1, halved
+ * every 20, 100 iterations):
+ *   q    <- grad u / sqrt(|grad u|^2 + eps^2)
+ *   u    <- u - xi [c sum_k (u - f_k) / sqrt((u - f_k)^2 + eps^2) - lambda div q]
+ *   ubar <- u;  p is not touched; u is not clamped.
+ * Restructuring stays a separate call (ofu_restructure).  Asynchronous.
+ * EINVAL for n < 0, t0 < 0, eps <= 0, xi0 <= 0 or halve_every < 1 (or NaN);
+ * ESTATE before ofu_integrate_frames. */
+ofu_status ofu_descend(ofu_ctx* ctx, int32_t n, int32_t t0, double eps, double xi0,
+                       int32_t halve_every);
+
 /* ---- inspection and test hooks ----------------------------------------- */
 
 typedef enum {

@@ -20,7 +20,7 @@ Modules
   dense      an independent dense-grid solver (the fully refined special case)
   mlp        the per-leaf warm-start network (features, forward, gradient, Adam)
   descent    the paper's own solver: gradient descent on the eps-L1 energy
-             (Eq. 4-6, Sec. 4 schedule); no CUDA counterpart yet
+             (Eq. 4-6, Sec. 4 schedule)
 
 Parity unpinned: nothing in the oracle reproduces the paper's printed results
 (Tables 1-2, the accuracy figures), which need the paper's datasets and its

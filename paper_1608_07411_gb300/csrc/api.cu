@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "descent.cuh"
 #include "ofu_internal.cuh"
 
 namespace ofu {
@@ -26,7 +27,7 @@ thread_local std::string g_create_error;
 // Persistent device buffers by role (content not kept across growth).
 enum Buf {
   B_SCAN, B_U0, B_PYR, B_FLAGS, B_POS, B_CNT, B_OVFC, B_CLS, B_OUTC, B_JL, B_SRC, B_LIST,
-  B_SMALL, B_PART, B_BIG, B_LONGQ, B_FWD, B_AUX, B_FULL, B_PENDQ, B_NUM
+  B_SMALL, B_PART, B_BIG, B_LONGQ, B_FWD, B_AUX, B_FULL, B_PENDQ, B_Q, B_NUM
 };
 
 struct Bufs {
@@ -608,6 +609,27 @@ ofu_status ofu_restructure(ofu_ctx* ctx, int64_t* n_split, int64_t* n_join, int6
   if (n_split) *n_split = ns;
   if (n_join) *n_join = nj;
   if (n_leaves) *n_leaves = n_new;
+  return OFU_OK;
+}
+
+ofu_status ofu_descend(ofu_ctx* ctx, int32_t n, int32_t t0, double eps, double xi0,
+                       int32_t halve_every) {
+  ST(check_built(ctx));
+  if (n < 0 || t0 < 0) return fail(ctx, OFU_EINVAL, "descend: n and t0 must be >= 0");
+  if (!(eps > 0) || !(xi0 > 0) || !std::isfinite(eps) || !std::isfinite(xi0))
+    return fail(ctx, OFU_EINVAL, "descend: eps and xi0 must be finite and > 0");
+  if (halve_every < 1) return fail(ctx, OFU_EINVAL, "descend: halve_every must be >= 1");
+  Leaves& L = ctx->L[ctx->cur];
+  float* q;
+  ST(ensure(ctx, B_Q, size_t(3 * L.cap), &q));
+  const View v = view_of(ctx);
+  for (int32_t i = 0; i < n; ++i) {
+    const int64_t t = int64_t(t0) + i;
+    const double xi = xi0 * std::ldexp(1.0, -int(std::min<int64_t>(t / halve_every, 2000)));
+    CU(launch_descent_step(v, L.u, L.ubar, q, L.soff, ctx->samp[ctx->cur], ctx->prm.sample_fp16 != 0,
+                           float(eps), float(xi), float(ctx->prm.lambda), float(ctx->prm.gamma),
+                           ctx->stream));
+  }
   return OFU_OK;
 }
 

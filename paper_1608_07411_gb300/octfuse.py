@@ -66,6 +66,7 @@ _SIGS = {
     "ofu_last_error": (ctypes.c_char_p, [_vp]),
     "ofu_integrate_frames": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _vp]),
     "ofu_iterate": (_i32, [_vp, _i32]),
+    "ofu_descend": (_i32, [_vp, _i32, _i32, _d, _d, _i32]),
     "ofu_restructure": (_i32, [_vp, _P64, _P64, _P64]),
     "ofu_energy": (_i32, [_vp, _PD, _PD, _PD]),
     "ofu_num_leaves": (_i32, [_vp, _P64]),
@@ -189,6 +190,11 @@ def ofu_integrate_frames(ctx, F, H, W, depth, intr, pose) -> None:
 
 def ofu_iterate(ctx, n: int) -> None:
     _check(ctx, load().ofu_iterate(ctx, n))
+
+
+def ofu_descend(ctx, n: int, t0: int = 0, eps: float = 1e-3, xi0: float = 0.1,
+                halve_every: int = 20) -> None:
+    _check(ctx, load().ofu_descend(ctx, n, t0, eps, xi0, halve_every))
 
 
 def ofu_restructure(ctx):
@@ -389,6 +395,9 @@ class Octree:
 
     def iterate(self, n):
         ofu_iterate(self.ctx, n)
+
+    def descend(self, n, t0=0, eps=1e-3, xi0=0.1, halve_every=20):
+        ofu_descend(self.ctx, n, t0, eps, xi0, halve_every)
 
     def restructure(self):
         return ofu_restructure(self.ctx)
