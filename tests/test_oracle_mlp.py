@@ -94,3 +94,41 @@ def test_features_definition():
     np.testing.assert_array_equal(X[b, 33], st.u[b])
     one = np.nonzero(cnt == 1)[0]
     np.testing.assert_array_equal(X[one, 33], st.u[idx[off[one]]])
+
+
+def test_warm_start_fallbacks():
+    """The network's output where W > 0 and finite; the median otherwise."""
+    s = make_scene("sphere", 2, frames=6, width=64, height=48, max_depth=4)
+    st = solver.initial_state(s)
+    st.W[::7] = 0                     # some leaves seen by no frame
+    st.fs[::7] = np.nan
+    th = mlp.init(5)
+    y, _ = mlp.forward(th, mlp.features(st))
+    u = mlp.warm_start(st, th)
+    seen = st.W > 0
+    assert seen.any() and (~seen).any()
+    np.testing.assert_array_equal(u[seen], y[seen])
+    np.testing.assert_array_equal(u[~seen], st.u[~seen])
+    bad = th.copy()
+    bad[:] = np.nan
+    np.testing.assert_array_equal(mlp.warm_start(st, bad), st.u)
+
+
+def test_dual_start_closed_form_on_a_ramp():
+    """u = a x on a fully refined grid: grad u = (a, 0, 0) inside and 0 on the
+    far x boundary, so p = lambda (sign a, 0, 0) where |a| >= g0, 0 where the
+    ramp is flatter than g0 or on the boundary layer."""
+    s = make_scene("sphere", 2, frames=2, width=16, height=12, max_depth=3, spread_tau=-1.0)
+    st = solver.initial_state(s)
+    from oracle import morton
+    x, _, _ = morton.decode(st.keys, s.max_depth)
+    n = 1 << s.max_depth
+    for a, g0 in ((0.2, 0.05), (-0.2, 0.05), (0.01, 0.05)):
+        p, g = mlp.dual_start(st, a * x.astype(np.float64), g0)
+        inner = x < n - 1
+        np.testing.assert_allclose(g[inner], abs(a), rtol=1e-14)
+        np.testing.assert_array_equal(g[~inner], 0.0)
+        want = st.lam * np.sign(a) if abs(a) >= g0 else 0.0
+        np.testing.assert_allclose(p[inner, 0], want, rtol=1e-14)
+        np.testing.assert_array_equal(p[:, 1:], 0.0)
+        np.testing.assert_array_equal(p[~inner], 0.0)
