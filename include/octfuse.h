@@ -21,7 +21,9 @@
  *     split, subtrees whose leaves all hold |u| > tau_join with one sign are
  *     joined.
  * The minimiser here is the first-order primal-dual method the paper names as
- * future work (Sec. 5, Chambolle & Pock), applied to the exact L1 energy.
+ * future work (Sec. 5, Chambolle & Pock), applied to the exact L1 energy;
+ * ofu_descend runs the paper's own gradient descent on the eps-L1 energy
+ * (Eq. 4-6) on the same leaves and operators.
  *
  * Data layout (all owned by the context, in HBM):
  *   leaves sorted by Morton key of their minimum corner in finest-voxel units
@@ -35,8 +37,12 @@
  *
  * Errors: every call returns an ofu_status; ofu_last_error() describes the
  * last failure.  OFU_EINVAL / OFU_ESTATE / OFU_ECAPACITY leave the context as
- * it was.  OFU_ECUDA poisons the context: only ofu_destroy is valid after it.
- * No call aborts the process or traps on the device.
+ * it was, except where a call has already replaced the frames or the
+ * structure when it finds the problem (ofu_integrate_frames when the
+ * construction exceeds a cap, ofu_load on a malformed file): the context then
+ * holds no octree until a call that builds one succeeds.  OFU_ECUDA and
+ * OFU_ENOMEM poison the context: only ofu_destroy is valid after them.  No
+ * call aborts the process or traps on the device.
  */
 #ifndef OCTFUSE_H
 #define OCTFUSE_H
@@ -83,8 +89,9 @@ void ofu_default_params(ofu_params* p);
 
 /* Creates an empty context on the current CUDA device.  `cuda_stream` is a
  * cudaStream_t (NULL = legacy default stream), borrowed for the context's
- * lifetime.  Device memory is allocated by the library (cudaMalloc) and
- * released by ofu_destroy.  EINVAL for out-of-range parameters. */
+ * lifetime.  Device memory is allocated by the library (cudaMalloc; see
+ * ofu_create_octree_ex for a caller's allocator) and released by
+ * ofu_destroy.  EINVAL for out-of-range parameters. */
 ofu_status ofu_create_octree(const ofu_params* params, void* cuda_stream, ofu_ctx** out);
 
 /* Device allocator supplied by the caller (for example a framework's caching
