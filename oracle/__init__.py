@@ -21,6 +21,7 @@ Modules
   mlp        the per-leaf warm-start network (features, forward, gradient, Adam)
   descent    the paper's own solver: gradient descent on the eps-L1 energy
              (Eq. 4-6, Sec. 4 schedule)
+  quantisation  Eq. 7 quantisation error between a dense and an octree field
 
 Parity unpinned: nothing in the oracle reproduces the paper's printed results
 (Tables 1-2, the accuracy figures), which need the paper's datasets and its
