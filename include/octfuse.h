@@ -199,6 +199,16 @@ ofu_status ofu_solve(ofu_ctx* ctx, int32_t iters, int32_t restructure_every, int
 ofu_status ofu_descend(ofu_ctx* ctx, int32_t n, int32_t t0, double eps, double xi0,
                        int32_t halve_every);
 
+/* Eq. 7 (Sec. 4.2, split and join): the quantisation error between a field
+ * on the finest voxels and the current leaves,
+ *   err = sum over leaves n of | u(n) - mean of fine over the voxels of n |.
+ * fine: host or device, float32 [n_fine], n_fine = 8^max_depth, indexed by the
+ * Morton key of each finest voxel -- the u of a fully refined run exported in
+ * key order.  err: host double.  Means are differences of float64 prefix
+ * sums; the terms are summed in a fixed order.  Synchronises.  EINVAL for
+ * NULL pointers or a wrong n_fine; ESTATE before ofu_integrate_frames. */
+ofu_status ofu_quantisation_error(ofu_ctx* ctx, const float* fine, int64_t n_fine, double* err);
+
 /* ---- inspection and test hooks ----------------------------------------- */
 
 typedef enum {

@@ -9,6 +9,7 @@
 
 #include "descent.cuh"
 #include "ofu_internal.cuh"
+#include "quant.cuh"
 
 namespace ofu {
 namespace {
@@ -27,7 +28,7 @@ thread_local std::string g_create_error;
 // Persistent device buffers by role (content not kept across growth).
 enum Buf {
   B_SCAN, B_U0, B_PYR, B_FLAGS, B_POS, B_CNT, B_OVFC, B_CLS, B_OUTC, B_JL, B_SRC, B_LIST,
-  B_SMALL, B_PART, B_BIG, B_LONGQ, B_FWD, B_AUX, B_FULL, B_PENDQ, B_Q, B_NUM
+  B_SMALL, B_PART, B_BIG, B_LONGQ, B_FWD, B_AUX, B_FULL, B_PENDQ, B_Q, B_QF, B_QD, B_QT, B_NUM
 };
 
 struct Bufs {
@@ -630,6 +631,24 @@ ofu_status ofu_descend(ofu_ctx* ctx, int32_t n, int32_t t0, double eps, double x
                            float(eps), float(xi), float(ctx->prm.lambda), float(ctx->prm.gamma),
                            ctx->stream));
   }
+  return OFU_OK;
+}
+
+ofu_status ofu_quantisation_error(ofu_ctx* ctx, const float* fine, int64_t n_fine, double* err) {
+  ST(check_built(ctx));
+  const int64_t nf = int64_t(1) << (3 * ctx->prm.max_depth);
+  if (!fine || !err) return fail(ctx, OFU_EINVAL, "quantisation_error: fine and err must be non-NULL");
+  if (n_fine != nf)
+    return fail(ctx, OFU_EINVAL, "quantisation_error: fine must hold 8^max_depth values");
+  float* f;
+  double *cfine, *terms, *tmp;
+  ST(ensure(ctx, B_QF, size_t(nf), &f));
+  ST(ensure(ctx, B_QD, size_t(nf + 1), &cfine));
+  ST(ensure(ctx, B_QT, size_t(ctx->n + 1), &terms));
+  ST(ensure(ctx, B_SCAN, scan_tmp_items<double>(std::max(nf, ctx->n)), &tmp));
+  CU(cudaMemcpyAsync(f, fine, size_t(nf) * sizeof(float), cudaMemcpyDefault, ctx->stream));
+  CU(launch_quant_error(view_of(ctx), ctx->L[ctx->cur].u, f, cfine, terms, tmp, ctx->stream));
+  ST(read_back(ctx, terms + ctx->n, sizeof(double), err));
   return OFU_OK;
 }
 

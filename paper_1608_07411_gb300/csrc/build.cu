@@ -1369,6 +1369,8 @@ template size_t scan_tmp_items<uint32_t>(int64_t);
 template size_t scan_tmp_items<uint64_t>(int64_t);
 template cudaError_t scan_exclusive<uint32_t>(const uint32_t*, uint32_t*, int64_t, uint32_t*, cudaStream_t);
 template cudaError_t scan_exclusive<uint64_t>(const uint64_t*, uint64_t*, int64_t, uint64_t*, cudaStream_t);
+template size_t scan_tmp_items<double>(int64_t);
+template cudaError_t scan_exclusive<double>(const double*, double*, int64_t, double*, cudaStream_t);
 
 template <int P>
 static cudaError_t dense_u0_p(const float* depth, const Cam* cams, int F, int H, int W, Geo g,

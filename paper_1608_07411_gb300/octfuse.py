@@ -67,6 +67,7 @@ _SIGS = {
     "ofu_integrate_frames": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _vp]),
     "ofu_iterate": (_i32, [_vp, _i32]),
     "ofu_descend": (_i32, [_vp, _i32, _i32, _d, _d, _i32]),
+    "ofu_quantisation_error": (_i32, [_vp, _vp, _i64, _PD]),
     "ofu_restructure": (_i32, [_vp, _P64, _P64, _P64]),
     "ofu_energy": (_i32, [_vp, _PD, _PD, _PD]),
     "ofu_num_leaves": (_i32, [_vp, _P64]),
@@ -195,6 +196,12 @@ def ofu_iterate(ctx, n: int) -> None:
 def ofu_descend(ctx, n: int, t0: int = 0, eps: float = 1e-3, xi0: float = 0.1,
                 halve_every: int = 20) -> None:
     _check(ctx, load().ofu_descend(ctx, n, t0, eps, xi0, halve_every))
+
+
+def ofu_quantisation_error(ctx, fine, n_fine: int) -> float:
+    err = ctypes.c_double()
+    _check(ctx, load().ofu_quantisation_error(ctx, _ptr(fine), n_fine, ctypes.byref(err)))
+    return err.value
 
 
 def ofu_restructure(ctx):
@@ -398,6 +405,10 @@ class Octree:
 
     def descend(self, n, t0=0, eps=1e-3, xi0=0.1, halve_every=20):
         ofu_descend(self.ctx, n, t0, eps, xi0, halve_every)
+
+    def quantisation_error(self, fine):
+        fine = np.ascontiguousarray(fine, np.float32)
+        return ofu_quantisation_error(self.ctx, fine, fine.size)
 
     def restructure(self):
         return ofu_restructure(self.ctx)
