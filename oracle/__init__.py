@@ -22,6 +22,7 @@ Modules
   descent    the paper's own solver: gradient descent on the eps-L1 energy
              (Eq. 4-6, Sec. 4 schedule)
   quantisation  Eq. 7 quantisation error between a dense and an octree field
+  mesh       zero level set of the fused field as a triangle mesh (Sec. 3.3)
 
 Parity unpinned: nothing in the oracle reproduces the paper's printed results
 (Tables 1-2, the accuracy figures), which need the paper's datasets and its
