@@ -23,6 +23,7 @@ Modules
              (Eq. 4-6, Sec. 4 schedule)
   quantisation  Eq. 7 quantisation error between a dense and an octree field
   mesh       zero level set of the fused field as a triangle mesh (Sec. 3.3)
+  frames     per-frame TSDF octrees as the data-term source (Fig. 4, Table 1)
 
 Parity unpinned: nothing in the oracle reproduces the paper's printed results
 (Tables 1-2, the accuracy figures), which need the paper's datasets and its
