@@ -350,9 +350,12 @@ ofu_status ofu_warm_start(ofu_ctx* ctx, const ofu_mlp* net);
  * Scratch: a file-scope device array of 8192 x 2 + 3 doubles (about 128 KiB),
  * present on every GPU that loads the library until the process exits.  One
  * partial pair per block of 2048 leaves, so at most 16,777,216 leaves:
- * larger octrees get OFU_ECAPACITY with a message naming the limit.  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.
+ * larger octrees get OFU_ECAPACITY with a message naming the limit.  Every
+ * call looks up the array's device address (cudaGetSymbolAddress, which
+ * allocates nothing) with the context's device current; the device that was
+ * current at ofu_create_octree must be current here, else OFU_EINVAL.  The
+ * first call on a device may load the library's device code there, so make
+ * it before any stream capture.
  * All calls share the array and each overwrites it, so calls that overlap on
  * the GPU (several streams or threads at once) race and must be serialised
  * by the caller. */

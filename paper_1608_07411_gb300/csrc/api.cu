@@ -865,6 +865,11 @@ ofu_status ofu_energy_static(ofu_ctx* ctx, double* out3) {
     return fail(ctx, OFU_ECAPACITY, "energy_static: " + std::to_string(ctx->n) +
                                         " leaves exceed its fixed scratch limit of " +
                                         std::to_string(energy_static_max_leaves()) + " leaves");
+  int dev = -1;
+  CU(cudaGetDevice(&dev));
+  if (dev != ctx->device)
+    return fail(ctx, OFU_EINVAL, "energy_static: the context's device (" + std::to_string(ctx->device) +
+                                     ") must be the current device (" + std::to_string(dev) + ")");
   double* scratch = nullptr;
   CU(energy_static_scratch(&scratch));
   Leaves& L = ctx->L[ctx->cur];

@@ -10,8 +10,6 @@
 // divergence gathers from the -face lists and nothing is scattered.
 #include <math_constants.h>
 
-#include <mutex>
-
 #include "ofu_internal.cuh"
 
 namespace ofu {
@@ -591,21 +589,13 @@ int64_t energy_static_max_leaves() { return int64_t(kStaticEnergyBlocks) * kStat
 
 cudaError_t energy_static_scratch(double** ptr) {
   // Host code cannot use the array's name as a device address: look the
-  // address up once per device, with that device current.
-  static std::mutex mu;
-  static double* addr[64] = {};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  // address up with the device current.  The lookup is repeated on every call
+  // (it allocates nothing) so that a module reloaded after cudaDeviceReset is
+  // never written through a stale address.
+  void* a = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&a, g_energy_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
-    void* a = nullptr;
-    e = cudaGetSymbolAddress(&a, g_energy_scratch);
-    if (e != cudaSuccess) return e;
-    addr[dev] = static_cast<double*>(a);
-  }
-  *ptr = addr[dev];
+  *ptr = static_cast<double*>(a);
   return cudaSuccess;
 }
 

@@ -145,3 +145,40 @@ def test_join_to_root():
     u[5] = 0.995   # one opposite sign blocks the root and its octant
     nk, nl, *_ = octree.restructure(k, lv, u, np.zeros((64, 3)), dmax, 0.95, 0.99)
     assert len(nk) == 7 + 8 and np.sum(nl == 1) == 7
+
+
+@pytest.mark.parametrize("name,seed,dmax", [("torus_box", 3, 4), ("at_scale", 5, 4), ("torus_box", 8, 5)])
+def test_dense_u0_voxel_by_voxel(name, seed, dmax):
+    """dense_u0[x, y, z] is the median of the Eq. 1 samples at the centre of
+    finest voxel (x, y, z) (Sec. 3.1, Eq. 1), -1 where no frame observes it.
+
+    The centre is written out directly from the voxel's integer coordinates
+    (origin + (x + 1/2) * voxel edge, float32 as Eq. 1 is evaluated) rather
+    than through Morton keys, and the median is NumPy's, so a swapped or
+    reversed axis in the oracle's index arithmetic shows here.  The scenes
+    have no symmetry under an exchange of axes, which the last assertions
+    check, so a transposed field cannot pass by accident."""
+    from oracle import tsdf
+    from paper_1608_07411_gb300.scenes import make_scene
+    sc = make_scene(name, seed, frames=10, width=96, height=72, max_depth=dmax)
+    u0 = octree.dense_u0(sc.origin, sc.extent, dmax, sc.depth, sc.intr, sc.pose, sc.delta, sc.eta)
+    n = 1 << dmax
+    vox = np.float32(np.float32(sc.extent) / np.float32(n))
+    ax = np.arange(n)
+    gx, gy, gz = np.meshgrid(ax, ax, ax, indexing="ij")
+    idx = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], 1)
+    pts = np.empty(idx.shape, np.float32)
+    for k in range(3):
+        pts[:, k] = np.float32(sc.origin[k]) + (idx[:, k].astype(np.float32) + np.float32(0.5)) * vox
+    f = tsdf.samples(pts, sc.depth, sc.intr, sc.pose, sc.delta, sc.eta)
+    want = np.empty(len(idx))
+    for i in range(len(idx)):
+        obs = f[i][~np.isnan(f[i])]
+        want[i] = np.median(obs) if obs.size else -1.0
+    got = u0[idx[:, 0], idx[:, 1], idx[:, 2]]
+    np.testing.assert_array_equal(got, want)
+    # the field carries both signs and a band, and no axis exchange maps it to itself
+    assert (want > 0.5).any() and (want < -0.5).any() and (np.abs(want) < 0.5).any()
+    for perm in ((1, 0, 2), (2, 1, 0), (0, 2, 1), (1, 2, 0)):
+        assert not np.array_equal(u0, u0.transpose(perm)), perm
+    assert not np.array_equal(u0, u0[::-1]) and not np.array_equal(u0, u0[:, :, ::-1])
