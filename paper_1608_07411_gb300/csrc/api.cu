@@ -28,7 +28,8 @@ thread_local std::string g_create_error;
 // Persistent device buffers by role (content not kept across growth).
 enum Buf {
   B_SCAN, B_U0, B_PYR, B_FLAGS, B_POS, B_CNT, B_OVFC, B_CLS, B_OUTC, B_JL, B_SRC, B_LIST,
-  B_SMALL, B_PART, B_BIG, B_LONGQ, B_FWD, B_AUX, B_FULL, B_PENDQ, B_Q, B_QF, B_QD, B_QT, B_NUM
+  B_SMALL, B_PART, B_BIG, B_LONGQ, B_FWD, B_AUX, B_FULL, B_PENDQ, B_Q, B_QF, B_QD, B_QT, B_LFL,
+  B_NUM
 };
 
 struct Bufs {
@@ -176,6 +177,24 @@ Geo geo_of(const ofu_ctx* ctx) {
   return g;
 }
 
+// Heavy and list leaves of the current structure for the dual (or primal) step.
+LeafSets dual_sets(const ofu_ctx* ctx) {
+  LeafSets ls;
+  ls.heavy = ctx->heavy;
+  ls.n_heavy = ctx->n_heavy_dual;
+  ls.list = ctx->heavy + 2 * ctx->heavy_cap;
+  ls.n_list = ctx->n_list_dual;
+  return ls;
+}
+LeafSets primal_sets(const ofu_ctx* ctx) {
+  LeafSets ls;
+  ls.heavy = ctx->heavy + ctx->heavy_cap;
+  ls.n_heavy = ctx->n_heavy_primal;
+  ls.list = ctx->heavy + 3 * ctx->heavy_cap;
+  ls.n_list = ctx->n_list_primal;
+  return ls;
+}
+
 // Copies `bytes` from device to a pinned host staging area and waits.
 ofu_status read_back(ofu_ctx* ctx, const void* dev, size_t bytes, void* host) {
   CU(cudaMemcpyAsync(ctx->pinned, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
@@ -229,13 +248,14 @@ ofu_status rebuild_topology(ofu_ctx* ctx, const uint32_t* samples_total = nullpt
     ctx->heavy = nullptr;
     ctx->heavy_cap = 0;
     const int64_t cap = std::max<int64_t>(n + n / 4, 1024);
-    CU(dalloc(ctx, &ctx->heavy, 2 * size_t(cap) * sizeof(uint32_t)));
+    CU(dalloc(ctx, &ctx->heavy, 4 * size_t(cap) * sizeof(uint32_t)));
     ctx->heavy_cap = cap;
   }
   unsigned long long* nlong = reinterpret_cast<unsigned long long*>(small + 8);
   unsigned long long* npend = reinterpret_cast<unsigned long long*>(small + 11);
-  uint64_t *hflags, *htmp;
+  uint64_t *hflags, *lflags, *htmp;
   ST(ensure(ctx, B_CLS, size_t(n + 1), &hflags));
+  ST(ensure(ctx, B_LFL, size_t(n + 1), &lflags));
   ST(ensure(ctx, B_OUTC, scan_tmp_items<uint64_t>(n) * 2, &htmp));
   if (carry.nbr) {
     ST(ensure(ctx, B_AUX, size_t(6 * n), &carry.aux));
@@ -244,19 +264,23 @@ ofu_status rebuild_topology(ofu_ctx* ctx, const uint32_t* samples_total = nullpt
   Leaves& L = ctx->L[ctx->cur];
   View v = view_of(ctx);
   CU(launch_nbr_count(v, carry, L.nbr, ovfc, longq, nlong, pendq, npend, ctx->stream));
-  CU(launch_heavy(v, ovfc, hflags, htmp, ctx->heavy, ctx->heavy + ctx->heavy_cap, ctx->stream));
+  CU(launch_leaf_sets(v, ovfc, hflags, lflags, htmp, ctx->heavy, ctx->heavy_cap, ctx->stream));
   CU(scan_exclusive<uint32_t>(ovfc, ovfc, 6 * n, tmp, ctx->stream));
-  // one read-back: packed heavy counts (slot 9), [list total, samples] (slot 10)
+  // one read-back: packed heavy counts (slot 9), [list total, samples] (slot 10),
+  // packed list-leaf counts (slot 13)
   CU(cudaMemcpyAsync(small + 9, hflags + n, sizeof(uint64_t), cudaMemcpyDeviceToDevice, ctx->stream));
+  CU(cudaMemcpyAsync(small + 13, lflags + n, sizeof(uint64_t), cudaMemcpyDeviceToDevice, ctx->stream));
   CU(cudaMemcpyAsync(reinterpret_cast<uint32_t*>(small + 10), ovfc + 6 * n, sizeof(uint32_t),
                      cudaMemcpyDeviceToDevice, ctx->stream));
   if (samples_total)
     CU(cudaMemcpyAsync(reinterpret_cast<uint32_t*>(small + 10) + 1, samples_total, sizeof(uint32_t),
                        cudaMemcpyDeviceToDevice, ctx->stream));
-  uint64_t hs[2];
-  ST(read_back(ctx, small + 9, 2 * sizeof(uint64_t), hs));
+  uint64_t hs[5];
+  ST(read_back(ctx, small + 9, 5 * sizeof(uint64_t), hs));
   ctx->n_heavy_dual = int(hs[0] & 0xffffffffu);
   ctx->n_heavy_primal = int(hs[0] >> 32);
+  ctx->n_list_dual = int(hs[4] & 0xffffffffu);
+  ctx->n_list_primal = int(hs[4] >> 32);
   const uint32_t total = uint32_t(hs[1] & 0xffffffffu);
   if (samples_total) ctx->n_samples = int64_t(hs[1] >> 32);
   if (int64_t(total) + 1 > L.ovf_cap) {
@@ -513,12 +537,10 @@ ofu_status ofu_iterate(ofu_ctx* ctx, int32_t n) {
       ctx->prof_used += 3;
       CU(cudaEventRecord(ev[0], ctx->stream));
     }
-    CU(launch_dual(v, L.ubar, L.p, L.sigma, float(ctx->prm.lambda), ctx->heavy,
-                   ctx->n_heavy_dual, ctx->stream));
+    CU(launch_dual(v, L.ubar, L.p, L.sigma, float(ctx->prm.lambda), dual_sets(ctx), ctx->stream));
     if (rec) CU(cudaEventRecord(ev[1], ctx->stream));
     CU(launch_primal(v, L.u, L.ubar, L.p, L.tau, L.soff, ctx->samp[ctx->cur], h16,
-                     float(ctx->prm.gamma), ctx->heavy + ctx->heavy_cap, ctx->n_heavy_primal,
-                     ctx->stream));
+                     float(ctx->prm.gamma), primal_sets(ctx), ctx->stream));
     if (rec) {
       CU(cudaEventRecord(ev[2], ctx->stream));
       ctx->prof_launches[0] += 1;
@@ -1068,8 +1090,8 @@ ofu_status ofu_warm_start(ofu_ctx* ctx, const ofu_mlp* net) {
   CU(cudaMemcpyAsync(L.u, L.ubar, size_t(ctx->n) * sizeof(float), cudaMemcpyDeviceToDevice,
                      ctx->stream));
   // dual start consistent with the new field: lambda n on its edges
-  CU(launch_dual_init(view_of(ctx), L.u, L.p, float(ctx->prm.lambda), kWarmEdge, ctx->heavy,
-                      ctx->n_heavy_dual, ctx->stream));
+  CU(launch_dual_init(view_of(ctx), L.u, L.p, float(ctx->prm.lambda), kWarmEdge, dual_sets(ctx),
+                      ctx->stream));
   return OFU_OK;
 }
 

@@ -985,32 +985,44 @@ __global__ void k_precond(View v, Carry cy, float* __restrict__ tau, float* __re
   tau[l] = col > 0.0f ? 1.0f / col : 1.0f;
 }
 
-// Heavy leaves from the list counts of the neighbour pass (1 + list length
-// per list face, 0 otherwise), before those counts are scanned: a packed flag
-// per leaf (bit 0 dual-heavy, bit 32 primal-heavy), scanned, then emitted in
-// leaf order, so the lists do not depend on scheduling.
-__global__ void k_heavy_flags(View v, const uint32_t* __restrict__ ovf_count,
-                              uint64_t* __restrict__ flags) {
+// Leaf classes from the list counts of the neighbour pass (1 + list length
+// per list face, 0 otherwise), before those counts are scanned: packed flags
+// per leaf (bit 0 dual, bit 32 primal) for heavy leaves and for list leaves,
+// scanned, then emitted in leaf order, so the sets do not depend on
+// scheduling.
+__global__ void k_class_flags(View v, const uint32_t* __restrict__ ovf_count,
+                              uint64_t* __restrict__ hflags, uint64_t* __restrict__ lflags) {
   const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (l >= v.n) return;
-  bool dual = false, primal = false;
+  bool hd = false, hp = false, ld = false, lp = false;
   for (int face = 0; face < 6; ++face) {
     const uint32_t c = ovf_count[int64_t(face) * v.n + l];
     if (c > uint32_t(kHeavy) + 1) {
-      primal = true;
-      if (face < 3) dual = true;
+      hp = true;
+      if (face < 3) hd = true;
+    } else if (c > 0) {
+      lp = true;
+      if (face < 3) ld = true;
     }
   }
-  flags[l] = (dual ? 1ull : 0ull) | (primal ? (1ull << 32) : 0ull);
+  ld &= !hd;
+  lp &= !hp;
+  hflags[l] = (hd ? 1ull : 0ull) | (hp ? (1ull << 32) : 0ull);
+  lflags[l] = (ld ? 1ull : 0ull) | (lp ? (1ull << 32) : 0ull);
 }
 
-__global__ void k_heavy_emit(int64_t n, const uint64_t* __restrict__ scan, uint32_t* __restrict__ hd,
-                             uint32_t* __restrict__ hp) {
+__global__ void k_class_emit(int64_t n, const uint64_t* __restrict__ hscan,
+                             const uint64_t* __restrict__ lscan, uint32_t* __restrict__ sets,
+                             int64_t cap) {
   const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (l >= n) return;
-  const uint64_t a = scan[l], b = scan[l + 1];
-  if ((b & 0xffffffffull) != (a & 0xffffffffull)) hd[a & 0xffffffffull] = uint32_t(l);
-  if ((b >> 32) != (a >> 32)) hp[a >> 32] = uint32_t(l);
+  const uint64_t* sc[2] = {hscan, lscan};
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const uint64_t a = sc[k][l], b = sc[k][l + 1];
+    if ((b & 0xffffffffull) != (a & 0xffffffffull)) sets[(2 * k) * cap + (a & 0xffffffffull)] = uint32_t(l);
+    if ((b >> 32) != (a >> 32)) sets[(2 * k + 1) * cap + (a >> 32)] = uint32_t(l);
+  }
 }
 
 __global__ void k_check_tiling(const uint64_t* __restrict__ key, const uint8_t* __restrict__ level,
@@ -1531,14 +1543,16 @@ cudaError_t launch_precond(View v, Carry cy, float* tau, float* sigma, const uin
   return cudaGetLastError();
 }
 
-cudaError_t launch_heavy(View v, const uint32_t* ovf_count, uint64_t* flags, uint64_t* tmp,
-                         uint32_t* heavy_dual, uint32_t* heavy_primal, cudaStream_t s) {
+cudaError_t launch_leaf_sets(View v, const uint32_t* ovf_count, uint64_t* hflags,
+                             uint64_t* lflags, uint64_t* tmp, uint32_t* sets, int64_t cap,
+                             cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
-  k_heavy_flags<<<blocks_for(v.n, 256), 256, 0, s>>>(v, ovf_count, flags);
+  k_class_flags<<<blocks_for(v.n, 256), 256, 0, s>>>(v, ovf_count, hflags, lflags);
   count_launches(1);
-  cudaError_t e = scan_exclusive<uint64_t>(flags, flags, v.n, tmp, s);
+  cudaError_t e = scan_exclusive<uint64_t>(hflags, hflags, v.n, tmp, s);
+  if (e == cudaSuccess) e = scan_exclusive<uint64_t>(lflags, lflags, v.n, tmp, s);
   if (e != cudaSuccess) return e;
-  k_heavy_emit<<<blocks_for(v.n, 256), 256, 0, s>>>(v.n, flags, heavy_dual, heavy_primal);
+  k_class_emit<<<blocks_for(v.n, 256), 256, 0, s>>>(v.n, hflags, lflags, sets, cap);
   count_launches(1);
   return cudaGetLastError();
 }

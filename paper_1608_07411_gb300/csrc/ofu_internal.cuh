@@ -163,6 +163,17 @@ struct View {
   const uint32_t* map; // finest voxel (Morton order) -> index of its leaf
 };
 
+// Leaves an iteration launch treats apart from the thread-per-leaf path:
+// heavy leaves (a face list longer than kHeavy, one block each) and list
+// leaves (finer neighbours on some face, none heavy; a thread each over this
+// compacted list so that their list walks share warps only with each other).
+struct LeafSets {
+  const uint32_t* heavy = nullptr;
+  int n_heavy = 0;
+  const uint32_t* list = nullptr;
+  int n_list = 0;
+};
+
 // The structure before a split/join pass, handed to the neighbour build of
 // the new one: a kept leaf (same key, same level) whose neighbours across a
 // face were all kept has the same neighbours afterwards, so its entry is
@@ -234,10 +245,12 @@ struct ofu_ctx {
   // finest voxel -> leaf index of the current structure (8^D entries)
   uint32_t* map = nullptr;
 
-  // heavy leaves of the current structure (see kHeavy)
-  uint32_t* heavy = nullptr;   // [0, cap): dual-heavy, [cap, 2 cap): primal-heavy
+  // leaf classes of the current structure (see kHeavy, LeafSets): [4][cap]
+  // heavy dual, heavy primal, list dual, list primal
+  uint32_t* heavy = nullptr;
   int64_t heavy_cap = 0;
   int n_heavy_dual = 0, n_heavy_primal = 0;
+  int n_list_dual = 0, n_list_primal = 0;
 
   // scratch (grown on demand)
   void* scratch = nullptr;
@@ -297,13 +310,17 @@ cudaError_t launch_leaf_fill(const uint64_t* key, const uint8_t* level, const ui
                              const Cam* cams, int F, int H, int W, Geo g, const uint32_t* soff,
                              void* samp, bool fp16, float* u, float* ubar, cudaStream_t s);
 
-// Heavy leaves: dual-heavy when a +face list exceeds kHeavy, primal-heavy
-// when any face list does, read from the unscanned neighbour-list counts and
-// listed in leaf order.  flags: n + 1 scratch words (flags[n] receives the
-// packed totals: dual count low 32 bits, primal count high 32 bits); tmp:
-// scan scratch for n.
-cudaError_t launch_heavy(View v, const uint32_t* ovf_count, uint64_t* flags, uint64_t* tmp,
-                         uint32_t* heavy_dual, uint32_t* heavy_primal, cudaStream_t s);
+// Leaf classes of the iteration kernels, read from the unscanned
+// neighbour-list counts and listed in leaf order: heavy (dual: a +face list
+// longer than kHeavy; primal: any face list longer than kHeavy) and list
+// leaves (dual: a +face list, none heavy; primal: any face list, none heavy).
+// sets: [4][cap] = heavy dual, heavy primal, list dual, list primal.
+// hflags, lflags: n + 1 scratch words each; hflags[n] and lflags[n] receive
+// the packed totals (dual count low 32 bits, primal count high 32 bits);
+// tmp: scan scratch for n.
+cudaError_t launch_leaf_sets(View v, const uint32_t* ovf_count, uint64_t* hflags,
+                             uint64_t* lflags, uint64_t* tmp, uint32_t* sets, int64_t cap,
+                             cudaStream_t s);
 
 // Face neighbours: count pass (long lists queued in longq and counted by a
 // block each), then the fill.
@@ -340,15 +357,16 @@ cudaError_t launch_copy_kept_samples(const int32_t* src, int64_t n, const uint32
                                      const void* old_samp, const uint32_t* new_soff,
                                      void* new_samp, bool fp16, cudaStream_t s);
 
-// Solver kernels.
+// Solver kernels.  `ls` names the heavy leaves and the list leaves of the
+// step (see LeafSets).
 cudaError_t launch_dual(View v, const float* ubar, float* p, const float* sigma, float lambda,
-                        const uint32_t* heavy, int n_heavy, cudaStream_t s);
+                        LeafSets ls, cudaStream_t s);
 // p = lambda g / |g| where |g| >= g0 (g the gradient of u), else 0.
 cudaError_t launch_dual_init(View v, const float* u, float* p, float lambda, float g0,
-                             const uint32_t* heavy, int n_heavy, cudaStream_t s);
+                             LeafSets ls, cudaStream_t s);
 cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const float* tau,
                           const uint32_t* soff, const void* samp, bool fp16, float gamma,
-                          const uint32_t* heavy, int n_heavy, cudaStream_t s);
+                          LeafSets ls, cudaStream_t s);
 size_t energy_tmp_bytes(int64_t n);
 cudaError_t launch_energy(View v, const float* u, const float* p, const uint32_t* soff,
                           const void* samp, bool fp16, double lambda, double gamma,

@@ -18,6 +18,11 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = 256;
+// Resident blocks per SM the iteration kernels are compiled for.  Without a
+// stated minimum the compiler caps them at 32 registers and spills (the heavy
+// path's block reductions share the register budget); 6 blocks (<= 42
+// registers) measured fastest over 4..8 on both the 256^3 and 512^3 workloads.
+constexpr int kIterMinBlocks = 6;
 
 __device__ __forceinline__ float edge_f(int D, int level) { return float(1u << (D - level)); }
 
@@ -80,18 +85,65 @@ __device__ __forceinline__ void dual_init_write(float* __restrict__ p, int64_t s
   p[2 * stride + l] = sc * g[2];
 }
 
+// Sum over one face's finer-neighbour list of w(level) * val(index), in list
+// order.  The entries are loaded four at a time and their values gathered
+// four at a time, so a list of c entries costs about 2 ceil(c / 4) dependent
+// loads instead of 2 c.
+template <typename WFn, typename VFn>
+__device__ __forceinline__ float list_sum(const int32_t* __restrict__ lst, int cnt, WFn w, VFn val) {
+  float acc = 0.0f;
+  for (int k0 = 0; k0 < cnt; k0 += 4) {
+    int32_t f[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) f[j] = k0 + j < cnt ? lst[k0 + j] : 0;
+    float x[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[j] = k0 + j < cnt ? val(entry_idx(f[j])) : 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (k0 + j < cnt) acc += w(entry_level(f[j])) * x[j];
+  }
+  return acc;
+}
+
+// Which leaf a thread of an iteration launch updates.  A launch is laid out as
+// [heavy blocks][list blocks][light blocks]: heavy leaves (a face list longer
+// than kHeavy) get a block each; "list" leaves (some face with finer
+// neighbours, none longer than kHeavy) a thread each over their compacted
+// index list, so their list walks do not hold up warps of plain leaves; every
+// other leaf a thread of the light blocks, which skip list leaves.  Returns
+// -1 for a thread with no leaf.
+struct Segments {
+  const uint32_t* heavy;
+  int n_heavy;
+  const uint32_t* list;
+  int n_list;
+};
+
+__device__ __forceinline__ int64_t segment_leaf(const Segments& sg, int64_t n, bool* is_list_leaf) {
+  const int lb = (sg.n_list + kThreads - 1) / kThreads;
+  const int b = int(blockIdx.x) - sg.n_heavy;
+  if (b < lb) {
+    const int j = b * kThreads + int(threadIdx.x);
+    *is_list_leaf = true;
+    return j < sg.n_list ? int64_t(sg.list[j]) : -1;
+  }
+  *is_list_leaf = false;
+  const int64_t l = int64_t(b - lb) * kThreads + threadIdx.x;
+  return l < n ? l : -1;
+}
+
 // INIT = false: the dual step p <- proj(p + sigma grad ubar).
 // INIT = true:  p <- dual_init_write(grad ubar) with threshold g0 (sigma unused).
 template <bool INIT>
-__global__ void __launch_bounds__(kThreads) k_dual(View v, const float* __restrict__ ubar,
+__global__ void __launch_bounds__(kThreads, kIterMinBlocks) k_dual(View v, const float* __restrict__ ubar,
                                                    float* __restrict__ p,
                                                    const float* __restrict__ sigma, float lambda,
-                                                   const uint32_t* __restrict__ heavy,
-                                                   int n_heavy_blocks, float g0) {
-  if (int(blockIdx.x) < n_heavy_blocks) {
+                                                   Segments sg, float g0) {
+  if (int(blockIdx.x) < sg.n_heavy) {
     // one heavy leaf per block; every thread takes part in the reductions
     __shared__ float red[kHeavyThreads / 32];
-    const int64_t l = heavy[blockIdx.x];
+    const int64_t l = sg.heavy[blockIdx.x];
     const float h = edge_f(v.D, v.level[l]);
     const float ul = ubar[l];
     float g[3];
@@ -121,84 +173,113 @@ __global__ void __launch_bounds__(kThreads) k_dual(View v, const float* __restri
     }
     return;
   }
-  // light path: one leaf per thread, 32-bit indices (N < 2^27), rows hoisted
-  const uint32_t l = (blockIdx.x - uint32_t(n_heavy_blocks)) * blockDim.x + threadIdx.x;
-  if (l >= uint32_t(v.n)) return;
+  bool listed;
+  const int64_t l = segment_leaf(sg, v.n, &listed);
+  if (l < 0) return;
   const size_t st = size_t(v.stride);
+  // every load that does not depend on another is issued before any branch
   const int32_t e[3] = {v.nbr[l], v.nbr[st + l], v.nbr[2 * st + l]};
-  const float h = edge_f(v.D, v.level[l]);
+  const int lev = v.level[l];
+  const float h = edge_f(v.D, lev);
   const float ul = ubar[l];
+  const float q[3] = {p[l], p[st + l], p[2 * st + l]};
+  const float sl = INIT ? 0.0f : sigma[l];
   float g[3];
+  if (!listed) {
+    // light path: single entries only; a list leaf's lane gathers its own
+    // value (harmless) and writes nothing (its list thread does)
+    float x[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    float acc = 0.0f;
-    if (e[d] >= 0) {
-      // same or coarser neighbour: alpha = 1
-      acc = (ubar[entry_idx(e[d])] - ul) * inv_delta(h, edge_f(v.D, entry_level(e[d])));
-    } else if (e[d] != kEmpty) {
-      const uint32_t s0 = list_start(e[d]);
-      const int cnt = v.ovf[s0];
-      if (cnt > kHeavy) return;   // updated by a heavy block
-      for (int k = 0; k < cnt; ++k) {
-        const int32_t f = v.ovf[s0 + 1 + k];
-        const float hm = edge_f(v.D, entry_level(f));
-        const float r = hm / h;
-        acc += r * r * (ubar[entry_idx(f)] - ul) * inv_delta(h, hm);
-      }
+    for (int d = 0; d < 3; ++d) x[d] = ubar[e[d] >= 0 ? entry_idx(e[d]) : uint32_t(l)];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float hm = edge_f(v.D, e[d] >= 0 ? entry_level(e[d]) : lev);
+      g[d] = e[d] >= 0 ? (x[d] - ul) * inv_delta(h, hm) : 0.0f;
     }
-    g[d] = acc;
+    if (is_list(e[0]) || is_list(e[1]) || is_list(e[2])) return;
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float acc = 0.0f;
+      if (e[d] >= 0) {
+        // same or coarser neighbour: alpha = 1
+        acc = (ubar[entry_idx(e[d])] - ul) * inv_delta(h, edge_f(v.D, entry_level(e[d])));
+      } else if (e[d] != kEmpty) {
+        // finer neighbours: alpha = (h_m / h)^2
+        const uint32_t s0 = list_start(e[d]);
+        acc = list_sum(
+            v.ovf + s0 + 1, v.ovf[s0],
+            [&](int lev) {
+              const float hm = edge_f(v.D, lev);
+              const float r = hm / h;
+              return r * r * inv_delta(h, hm);
+            },
+            [&](uint32_t m) { return ubar[m] - ul; });
+      }
+      g[d] = acc;
+    }
   }
-  if (INIT)
+  if (INIT) {
     dual_init_write(p, v.stride, l, g, lambda, g0);
-  else
-    dual_write(p, v.stride, l, sigma[l], g, lambda);
+  } else {
+    float r0 = q[0] + sl * g[0], r1 = q[1] + sl * g[1], r2 = q[2] + sl * g[2];
+    const float nrm = sqrtf(r0 * r0 + r1 * r1 + r2 * r2);
+    if (nrm > lambda) {
+      const float sc = lambda / nrm;
+      r0 *= sc;
+      r1 *= sc;
+      r2 *= sc;
+    }
+    p[l] = r0;
+    p[st + l] = r1;
+    p[2 * st + l] = r2;
+  }
 }
 
-// Divergence of p at leaf l (gathers only).  Returns false, without a
-// result, when a face list is longer than kHeavy (a heavy block owns it).
-__device__ __forceinline__ bool divergence(const View& v, const float* __restrict__ p, int64_t l,
-                                           float h, float* out) {
+// Divergence of p at a list leaf l (gathers only; face lists of at most
+// kHeavy entries); q = p(l).
+__device__ __forceinline__ float divergence(const View& v, const float* __restrict__ p, int64_t l,
+                                            float h, const int32_t e[6], const float q[3]) {
   float dv = 0.0f;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const int32_t e = v.nbr[int64_t(d) * v.stride + l];
     float coef = 0.0f;
-    if (e >= 0) {
-      coef = inv_delta(h, edge_f(v.D, entry_level(e)));
-    } else if (e != kEmpty) {
-      const uint32_t st = list_start(e);
+    if (e[d] >= 0) {
+      coef = inv_delta(h, edge_f(v.D, entry_level(e[d])));
+    } else if (e[d] != kEmpty) {
+      const uint32_t st = list_start(e[d]);
+      const int32_t* lst = v.ovf + st + 1;
       const int cnt = v.ovf[st];
-      if (cnt > kHeavy) return false;
       for (int k = 0; k < cnt; ++k) {
-        const float hm = edge_f(v.D, entry_level(v.ovf[st + 1 + k]));
+        const float hm = edge_f(v.D, entry_level(lst[k]));
         const float r = hm / h;
         coef += r * r * inv_delta(h, hm);
       }
     }
-    dv += coef * p[int64_t(d) * v.stride + l];
+    dv += coef * q[d];
   }
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const int32_t e = v.nbr[int64_t(3 + d) * v.stride + l];
-    if (e >= 0) {
+    const int32_t ed = e[3 + d];
+    const float* pd = p + int64_t(d) * v.stride;
+    if (ed >= 0) {
       // same or coarser n: (h_n^3 / h^3) (h / h_n)^2 / Delta = (h_n / h) / Delta
-      const float hn = edge_f(v.D, entry_level(e));
-      dv -= (hn / h) * inv_delta(h, hn) * p[int64_t(d) * v.stride + entry_idx(e)];
-    } else if (e != kEmpty) {
+      const float hn = edge_f(v.D, entry_level(ed));
+      dv -= (hn / h) * inv_delta(h, hn) * pd[entry_idx(ed)];
+    } else if (ed != kEmpty) {
       // finer n: alpha = 1, weight (h_n / h)^3 / Delta
-      const uint32_t st = list_start(e);
-      const int cnt = v.ovf[st];
-      if (cnt > kHeavy) return false;
-      for (int k = 0; k < cnt; ++k) {
-        const int32_t f = v.ovf[st + 1 + k];
-        const float hn = edge_f(v.D, entry_level(f));
-        const float r = hn / h;
-        dv -= r * r * r * inv_delta(h, hn) * p[int64_t(d) * v.stride + entry_idx(f)];
-      }
+      const uint32_t st = list_start(ed);
+      dv -= list_sum(
+          v.ovf + st + 1, v.ovf[st],
+          [&](int lev) {
+            const float hn = edge_f(v.D, lev);
+            const float r = hn / h;
+            return r * r * r * inv_delta(h, hn);
+          },
+          [&](uint32_t m) { return pd[m]; });
     }
   }
-  *out = dv;
-  return true;
+  return dv;
 }
 
 // The same divergence by one block (kHeavyThreads threads) of a heavy leaf;
@@ -248,24 +329,28 @@ __device__ float divergence_block(const View& v, const float* __restrict__ p, in
 // Prox of the data term: argmin_x (x - v)^2 / (2 tau) + c sum_k |x - f_k| is
 // the median of {f_k} and {v + t (W - 2k)}_{k=0..W}, t = tau c.  With the
 // samples sorted it is clamp(b_k*, f_(k*-1), f_k*) (0-based f, f_-1 = -inf,
-// f_W = +inf) where k* is the number of k with f_k < b_k = v + t (W - 2k);
-// that predicate holds for a prefix of k (f rises, b falls), so counting it
-// in one pass over the samples finds k*.  The pass has no data-dependent
-// addresses: every sample load is issued independently.
+// f_W = +inf) where k* is the number of k with f_k < b_k = v + t (W - 2k).
+// That predicate holds exactly for a prefix of k (f rises, b falls, and the
+// rounded b_k still falls), so k* is found by bisection in ceil(log2(W + 1))
+// probes.  The last probe that held is f_(k*-1), the last that failed is
+// f_k*, so no sample is loaded twice.
 template <typename T>
 __device__ __forceinline__ float prox_l1(const T* __restrict__ f, int W, float v, float t) {
-  int ks = 0;
-  float lo = -CUDART_INF_F, hi = CUDART_INF_F;
-#pragma unroll 4
-  for (int k = 0; k < W; ++k) {
-    const float fk = load_sample(f, k);
-    const bool below = fk < v + t * float(W - 2 * k);
-    ks += below;
-    lo = below ? fk : lo;
-    hi = (!below && hi == CUDART_INF_F) ? fk : hi;
+  int lo = 0, hi = W;
+  float flo = -CUDART_INF_F, fhi = CUDART_INF_F;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const float fm = load_sample(f, mid);
+    if (fm < __fmaf_rn(t, float(W - 2 * mid), v)) {
+      lo = mid + 1;
+      flo = fm;
+    } else {
+      hi = mid;
+      fhi = fm;
+    }
   }
-  const float b = v + t * float(W - 2 * ks);
-  return fmaxf(lo, fminf(b, hi));
+  const float b = __fmaf_rn(t, float(W - 2 * lo), v);
+  return fmaxf(flo, fminf(b, fhi));
 }
 
 template <typename T>
@@ -282,17 +367,16 @@ __device__ __forceinline__ void primal_write(float* __restrict__ u, float* __res
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_primal(View v, float* __restrict__ u,
+__global__ void __launch_bounds__(kThreads, kIterMinBlocks) k_primal(View v, float* __restrict__ u,
                                                      float* __restrict__ ubar,
                                                      const float* __restrict__ p,
                                                      const float* __restrict__ tau,
                                                      const uint32_t* __restrict__ soff,
                                                      const T* __restrict__ samp, float gamma,
-                                                     const uint32_t* __restrict__ heavy,
-                                                     int n_heavy_blocks) {
-  if (int(blockIdx.x) < n_heavy_blocks) {
+                                                     Segments sg) {
+  if (int(blockIdx.x) < sg.n_heavy) {
     __shared__ float red[kHeavyThreads / 32];
-    const int64_t l = heavy[blockIdx.x];
+    const int64_t l = sg.heavy[blockIdx.x];
     const float h = edge_f(v.D, v.level[l]);
     const float dv = divergence_block(v, p, l, h, red);
     if (threadIdx.x == 0) {
@@ -302,14 +386,54 @@ __global__ void __launch_bounds__(kThreads) k_primal(View v, float* __restrict__
     }
     return;
   }
-  const int64_t l = int64_t(blockIdx.x - n_heavy_blocks) * blockDim.x + threadIdx.x;
-  if (l >= v.n) return;
-  const float h = edge_f(v.D, v.level[l]);
-  float dv;
-  if (!divergence(v, p, l, h, &dv)) return;   // updated by a heavy block
+  bool listed;
+  const int64_t l = segment_leaf(sg, v.n, &listed);
+  if (l < 0) return;
+  // every load that does not depend on another is issued before any branch
+  int32_t e[6];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) e[f] = v.nbr[int64_t(f) * v.stride + l];
+  const int lev = v.level[l];
+  const float h = edge_f(v.D, lev);
+  float q[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) q[d] = p[int64_t(d) * v.stride + l];
   const float tl = tau[l];
   const float ul = u[l];
-  primal_write(u, ubar, l, ul, ul + tl * dv, tl, soff, samp, gamma);
+  const uint32_t o = soff[l];
+  const int W = int(soff[l + 1] - o);
+  float dv;
+  if (!listed) {
+    // light path: single entries only; a list leaf's lane gathers its own
+    // p (harmless) and writes nothing (its list thread does)
+    float pn[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      pn[d] = p[int64_t(d) * v.stride + (e[3 + d] >= 0 ? entry_idx(e[3 + d]) : uint32_t(l))];
+    dv = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float hm = edge_f(v.D, e[d] >= 0 ? entry_level(e[d]) : lev);
+      dv += (e[d] >= 0 ? inv_delta(h, hm) : 0.0f) * q[d];
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      // same or coarser n: (h_n^3 / h^3) (h / h_n)^2 / Delta = (h_n / h) / Delta
+      const float hn = edge_f(v.D, e[3 + d] >= 0 ? entry_level(e[3 + d]) : lev);
+      dv -= e[3 + d] >= 0 ? (hn / h) * inv_delta(h, hn) * pn[d] : 0.0f;
+    }
+    bool any = false;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) any |= is_list(e[f]);
+    if (any) return;
+  } else {
+    dv = divergence(v, p, l, h, e, q);
+  }
+  const float x = ul + tl * dv;
+  const float t = tl / (float(W) + gamma);
+  const float un = fminf(fmaxf(prox_l1(samp + o, W, x, t), -1.0f), 1.0f);
+  u[l] = un;
+  ubar[l] = 2.0f * un - ul;
 }
 
 // ---------------------------------------------------------------------------
@@ -509,37 +633,40 @@ inline unsigned blocks_for(int64_t n, int threads) { return unsigned((n + thread
 
 }  // namespace
 
+inline unsigned grid_of(int64_t n, const Segments& sg) {
+  return blocks_for(n, kThreads) + blocks_for(sg.n_list, kThreads) + unsigned(sg.n_heavy);
+}
+
 cudaError_t launch_dual(View v, const float* ubar, float* p, const float* sigma, float lambda,
-                        const uint32_t* heavy, int n_heavy, cudaStream_t s) {
+                        LeafSets ls, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
-  k_dual<false><<<blocks_for(v.n, kThreads) + n_heavy, kThreads, 0, s>>>(v, ubar, p, sigma, lambda,
-                                                                          heavy, n_heavy, 0.0f);
+  const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
+  k_dual<false><<<grid_of(v.n, sg), kThreads, 0, s>>>(v, ubar, p, sigma, lambda, sg, 0.0f);
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_dual_init(View v, const float* u, float* p, float lambda, float g0,
-                             const uint32_t* heavy, int n_heavy, cudaStream_t s) {
+cudaError_t launch_dual_init(View v, const float* u, float* p, float lambda, float g0, LeafSets ls,
+                             cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
-  k_dual<true><<<blocks_for(v.n, kThreads) + n_heavy, kThreads, 0, s>>>(v, u, p, nullptr, lambda,
-                                                                         heavy, n_heavy, g0);
+  const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
+  k_dual<true><<<grid_of(v.n, sg), kThreads, 0, s>>>(v, u, p, nullptr, lambda, sg, g0);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const float* tau,
                           const uint32_t* soff, const void* samp, bool fp16, float gamma,
-                          const uint32_t* heavy, int n_heavy, cudaStream_t s) {
+                          LeafSets ls, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
-  const unsigned nb = blocks_for(v.n, kThreads) + n_heavy;
+  const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
+  const unsigned nb = grid_of(v.n, sg);
   if (fp16)
     k_primal<__half><<<nb, kThreads, 0, s>>>(v, u, ubar, p, tau, soff,
-                                             reinterpret_cast<const __half*>(samp), gamma, heavy,
-                                             n_heavy);
+                                             reinterpret_cast<const __half*>(samp), gamma, sg);
   else
     k_primal<float><<<nb, kThreads, 0, s>>>(v, u, ubar, p, tau, soff,
-                                            reinterpret_cast<const float*>(samp), gamma, heavy,
-                                            n_heavy);
+                                            reinterpret_cast<const float*>(samp), gamma, sg);
   count_launches(1);
   return cudaGetLastError();
 }
