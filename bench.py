@@ -1,11 +1,14 @@
 #!/usr/bin/env python
-"""Benchmark: octree TV-L1 fusion of the torus/box workload on GB300.
+"""Benchmark: octree TV-L1 fusion on GB300.
 
 One step = the whole hot path on one scan: Eq. 1/2 construction and leaf
 integration from device-resident frames (ofu_integrate_frames), then the
-workload's primal-dual iterations with split/join every 10 iterations and a
-final float64 energy (ofu_solve).  The metric is leaf-iterations per second
-(sum over iterations of the leaf count, divided by the step time).
+primal-dual iterations with split/join every 10 iterations until the
+workload's stopping rule (ofu_solve), which for the default workload (5
+seeded primitives, 100 views 640x480, D_max = 9) is a relative primal-dual gap
+below 1e-5 checked in float64 every 10 iterations, with an iteration cap.  The
+metric is leaf-iterations per second (sum over iterations of the leaf count,
+divided by the step time).
 
 Prints one JSON line.  Under torchrun every rank fuses its own seeded scan
 (independent problems: weak scaling, no collective on the data path); the
@@ -21,6 +24,7 @@ import dataclasses
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -33,15 +37,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "leaf-iterations/s"
 WORKLOAD_TEXT = {
+    "at_scale": "5 seeded spheres/tori/boxes in a 2 m scene, 100 depth maps 640x480 (Fibonacci sphere "
+                "of cameras at 3 m, fx=fy=600), noise 0.0015 z^2 m, D_max=9 (512^3), primal-dual "
+                "iterations with split/join every 10 during the first 500, then on that structure until "
+                "the relative gap < 1e-5 (checked every 50, cap 20000)",
     "torus_box": "torus R=0.3 r=0.08 united with an axis-aligned 0.3^3 box, 32 depth maps 640x480 "
                  "(seeded Fibonacci sphere of cameras at 1.2 m, fx=fy=600), noise 2 mm + 1% outliers, "
                  "D_max=8 (256^3), 500 primal-dual iterations, split/join every 10",
     "sphere": "sphere r=0.4, 8 depth maps 160x120 on a ring at 1.5 m, noise 1 mm, D_max=6, "
               "200 iterations, split/join every 10",
-    "at_scale": "5 seeded spheres/tori/boxes in a 2 m scene, 100 depth maps 640x480, D_max=9",
 }
-# world point whose level-2 octree node is the oracle's bounded sample
-CROP_POINT = {"torus_box": (0.3, 0.0, 0.0), "sphere": (0.4, 0.0, 0.0), "at_scale": (0.0, 0.0, 0.0)}
+# the oracle's bounded sample: the octree node (level, around a world point)
+# that the oracle builds and iterates on its own
+CROP = {"torus_box": ((0.3, 0.0, 0.0), 2), "sphere": ((0.4, 0.0, 0.0), 2),
+        "at_scale": ((0.0, 0.0, 0.0), 3)}
 
 
 def args_():
@@ -50,14 +59,42 @@ def args_():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--workload", default="torus_box", choices=tuple(WORKLOAD_TEXT))
+    ap.add_argument("--workload", default="at_scale", choices=tuple(WORKLOAD_TEXT))
+    ap.add_argument("--second", default="torus_box", choices=tuple(WORKLOAD_TEXT) + ("none",),
+                    help="a second workload measured the same way and reported inside the line")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--fp16", action="store_true", help="store Eq. 1 samples as float16")
-    ap.add_argument("--iters", type=int, default=0, help="override the workload's iteration count")
+    ap.add_argument("--iters", type=int, default=0, help="override the workload's iteration cap")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-tte", action="store_true", help="skip the time-to-energy measurement")
+    ap.add_argument("--no-precision", action="store_true", help="skip the float16/float32 field errors")
     return ap.parse_args()
+
+
+def stop_rule(a, scene):
+    """The workload's solve: (iteration cap, restructure period, refinement
+    iterations, gap check period, gap tolerance).  With a gap tolerance the
+    solve splits/joins every `R` iterations during the first `refine`
+    iterations, then keeps that structure and iterates until the relative
+    gap is below the tolerance (checked every `check` iterations) or the cap."""
+    R = scene.restructure_every
+    tol = scene.gap_tol
+    refine = scene.refine_iters if tol > 0 else 0
+    check = scene.gap_check_every if tol > 0 else 0
+    return (a.iters or scene.iters), R, refine, check, tol
+
+
+def run_solve(of, ctx, rule):
+    """One solve by the rule of stop_rule: (iterations, leaf-iterations, energies)."""
+    cap, R, refine, check, tol = rule
+    if tol <= 0:
+        return of.ofu_solve(ctx, cap, R, 0, 0.0)
+    d1, l1, e = of.ofu_solve(ctx, min(refine, cap), R, 0, 0.0)
+    if cap <= refine:
+        return d1, l1, e
+    d2, l2, e = of.ofu_solve(ctx, cap - refine, 0, check, tol)
+    return d1 + d2, l1 + l2, e
 
 
 # ----------------------------------------------------------------------------
@@ -65,32 +102,60 @@ def args_():
 
 
 def oracle_crop(scene):
-    """The level-2 node (1/64 of the domain, 64^3 finest voxels at D_max=8)
-    around a surface point, as a scene of its own: the oracle builds that
-    node's subtree with its own construction and iterates on it."""
+    """A node of the octree (CROP: level and a world point inside it) as a
+    scene of its own: the oracle builds that node's subtree with its own
+    construction and iterates on it."""
     from oracle import solver
-    sub = 2
+    pt, sub = CROP[scene.name]
     node = scene.extent / (1 << sub)
-    pt = np.asarray(CROP_POINT[scene.name])
-    idx = np.clip(np.floor((pt - scene.origin) / node), 0, (1 << sub) - 1)
+    idx = np.clip(np.floor((np.asarray(pt) - scene.origin) / node), 0, (1 << sub) - 1)
     crop = dataclasses.replace(scene, origin=scene.origin + idx * node, extent=node,
                                max_depth=scene.max_depth - sub)
-    st = solver.initial_state(crop)
-    return crop, st
+    return crop, solver.initial_state(crop)
 
 
-def cpu_rate(scene, seconds):
+def _oracle_worker(args):
+    """Runs the oracle on a crop for `seconds` (one host process)."""
+    crop, seconds = args
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle import solver
-    t0 = time.perf_counter()
-    crop, st = oracle_crop(scene)
-    setup = time.perf_counter() - t0
-    it = 0
-    t0 = time.perf_counter()
+    st = solver.initial_state(crop)
+    it, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < seconds:
         solver.step(st, 5)
         it += 5
-    dt = time.perf_counter() - t0
-    return len(st.keys) * it / dt, len(st.keys), it, dt, setup
+    return len(st.keys) * it, time.perf_counter() - t0
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                low = ln.lower()
+                if low.startswith("model name") or low.startswith("cpu part") or low.startswith("hardware"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def cpu_rate(scene, seconds):
+    """Oracle throughput on the crop: one process, then one process per host
+    core (independent copies, summed), started with spawn."""
+    import multiprocessing as mp
+    t0 = time.perf_counter()
+    crop, st = oracle_crop(scene)
+    setup = time.perf_counter() - t0
+    work, dt = _oracle_worker((crop, seconds))
+    one = work / dt
+    cores = os.cpu_count() or 1
+    allc = None
+    if cores > 1:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_worker, [(crop, seconds)] * cores)
+        allc = sum(w / t for w, t in res)
+    return {"one_core": one, "all_cores": allc, "cores": cores, "leaves": len(st.keys),
+            "setup_s": setup, "seconds": seconds}
 
 
 def run_reference(a, scene):
@@ -105,23 +170,27 @@ def run_reference(a, scene):
         solver.step(st, per_step)
         times.append(time.perf_counter() - t0)
     value = len(st.keys) * per_step * a.steps / sum(times)
-    sample = (f"oracle (float64 NumPy/SciPy, single thread) on the level-2 node around "
-              f"{CROP_POINT[scene.name]} of the {scene.name} scan ({len(st.keys)} leaves of its own "
-              f"construction), {per_step} iterations per step")
+    pt, sub = CROP[scene.name]
+    sample = (f"oracle (float64 NumPy/SciPy, single thread) on the level-{sub} node around {pt} of the "
+              f"{scene.name} scan ({len(st.keys)} leaves of its own construction), {per_step} iterations "
+              f"per step")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * statistics.mean(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_of(a, scene, extra={"sample": sample}),
-        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host_cores": os.cpu_count(), "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def config_of(a, scene, extra=None):
+    cap, R, refine, check, tol = stop_rule(a, scene)
     cfg = {"workload": f"{scene.name}: {WORKLOAD_TEXT[scene.name]}", "seed": a.seed,
-           "iterations": a.iters or scene.iters, "restructure_every": scene.restructure_every,
+           "iteration_cap": cap, "restructure_every": R, "restructure_until": refine or cap,
+           "gap_check_every": check, "gap_tol": tol,
            "samples": "float16" if a.fp16 else "float32",
            "l2": "flushed before every step (256 MiB write)",
            "parallelism": f"replicas x{a.gpus} (independent scans)"}
@@ -182,6 +251,7 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------
+# roofline inputs
 
 
 def kernel_source_sha():
@@ -192,16 +262,17 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel, alg_bytes_per_launch):
-    """DRAM bytes per launch from the committed ncu summary, scaled to this
-    launch by algorithmic bytes; None when absent or the kernel changed."""
+def measured_traffic(kernel, workload, alg_bytes_per_launch):
+    """DRAM bytes per launch from the committed ncu summary of this kernel on
+    this workload, scaled to this launch by algorithmic bytes; None when
+    absent or when the kernel source changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             t = json.load(fh)
     except (OSError, ValueError):
         return None
-    rec = t.get(kernel)
+    rec = t.get(workload, {}).get(kernel)
     if not rec or rec.get("source_sha") != kernel_source_sha():
         return None
     return rec["dram_bytes_per_launch"] * alg_bytes_per_launch / rec["alg_bytes_per_launch"]
@@ -215,58 +286,287 @@ def peak_hbm():
         return 6800.0, "fallback"
 
 
-def time_to_energy(a, scene, of, stream, depth_d, intr_d, pose_d):
-    """Reference energy E* = primal energy of the plain float32 solve at the
-    workload's iteration count; then, per form, the device time (from the
-    frames, construction included) and iterations until the primal energy
-    first drops to E* (1 + 1e-4), checked after every restructure window."""
-    import torch
-    F, H, W = scene.depth.shape
-    R = scene.restructure_every
-    iters = a.iters or scene.iters
+# ----------------------------------------------------------------------------
+# GPU legs
 
+
+class Gpu:
+    """Device copies of one scan and the stream the library runs on."""
+
+    def __init__(self, scene, of, torch, dev):
+        self.scene, self.of, self.torch = scene, of, torch
+        self.stream = torch.cuda.current_stream()
+        self.depth = torch.from_numpy(scene.depth).to(dev)
+        self.intr = torch.from_numpy(scene.intr.copy()).to(dev)
+        self.pose = torch.from_numpy(scene.pose.reshape(-1, 16).copy()).to(dev)
+        self.F, self.H, self.W = scene.depth.shape
+
+    def ctx(self, fp16):
+        return self.of.ofu_create_octree(self.of.params_for(self.scene, sample_fp16=fp16),
+                                         self.stream.cuda_stream)
+
+    def integrate(self, c):
+        self.of.ofu_integrate_frames(c, self.F, self.H, self.W, self.depth.data_ptr(),
+                                     self.intr.data_ptr(), self.pose.data_ptr())
+
+    def event(self):
+        e = self.torch.cuda.Event(enable_timing=True)
+        e.record(self.stream)
+        return e
+
+
+def rel_gap(e):
+    return e[2] / max(abs(e[0]), 1.0)
+
+
+def measure(a, scene, of, torch, dev, flush, dist, fp16, with_e2e):
+    """Timed steps of one workload; returns the figures of the JSON line."""
+    g = Gpu(scene, of, torch, dev)
+    rule = stop_rule(a, scene)
+    tol = rule[4]
+    ctx = g.ctx(fp16)
+    info = []
+
+    def step():
+        c0 = g.event()
+        g.integrate(ctx)
+        c1 = g.event()
+        n0 = of.ofu_num_leaves(ctx)
+        s0 = of.ofu_export_field(ctx, of.FIELD_SAMPLES, None, 0)
+        done, li, e = run_solve(of, ctx, rule)
+        info.append({"n0": n0, "s0": s0, "iters": done, "li": li, "energy": e, "cons": (c0, c1)})
+        return li
+
+    for _ in range(max(a.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    info.clear()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = of.ofu_kernel_launches()
+    times, leaf_iters = [], 0
+    for _ in range(a.steps):
+        flush.zero_()
+        ev0 = g.event()
+        leaf_iters += step()
+        ev1 = g.event()
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+    torch.cuda.synchronize()
+    launches = of.ofu_kernel_launches() - l0
+    total_ms, work = aggregate(dist, sum(times), leaf_iters, dev)
+    last = info[-1]
+    out = {
+        "value": work / (total_ms / 1e3), "ms_per_step": total_ms / a.steps, "gpu_launches": launches,
+        "leaf_iterations_per_step": leaf_iters / a.steps,
+        "iterations": last["iters"], "final_energy": last["energy"], "rel_gap": rel_gap(last["energy"]),
+        "gap_tol": tol, "gap_reached": bool(tol > 0 and rel_gap(last["energy"]) < tol),
+        "leaves_initial": int(statistics.median(i["n0"] for i in info)),
+        "leaves_final": of.ofu_num_leaves(ctx),
+        "samples_initial": int(statistics.median(i["s0"] for i in info)),
+        "samples_final": of.ofu_export_field(ctx, of.FIELD_SAMPLES, None, 0),
+    }
+    cons_ms = statistics.median(c0.elapsed_time(c1) for c0, c1 in (i["cons"] for i in info))
+    evals = (8 ** scene.max_depth + 2 * out["leaves_initial"]) * g.F
+    out["construction"] = {"ms": cons_ms, "eq1_evaluations": evals,
+                           "eq1_evaluations_per_s": evals / (cons_ms * 1e-3),
+                           "share_of_step": cons_ms * a.steps / sum(times)}
+
+    # ---- one more step with per-launch events on the two iteration kernels
+    # (kept out of the timed steps above)
+    flush.zero_()
+    info.clear()
+    of.ofu_profile(ctx, max(rule[0], 1))
+    pe0 = g.event()
+    li_prof = step()
+    pe1 = g.event()
+    ms, nl, ab = of.ofu_profile_read(ctx)
+    of.ofu_profile(ctx, False)
+    prof_step_ms = pe0.elapsed_time(pe1)
+    timed_iters = int(nl[0])
+    assert timed_iters == info[-1]["iters"], "per-launch event pool smaller than the step"
+    out["profile"] = {"ms": list(ms), "launches": list(nl), "alg_bytes": list(ab),
+                      "leaf_iterations": li_prof, "step_ms": prof_step_ms}
+    out["iterate_only"] = {"value": li_prof / ((ms[0] + ms[1]) * 1e-3), "unit": METRIC,
+                           "kernels": ["k_dual", "k_primal"],
+                           "scope": "one profiled step after the timed ones (rank 0)",
+                           "share_of_step": (ms[0] + ms[1]) / prof_step_ms}
+
+    if with_e2e:
+        out["e2e"] = e2e(a, g, ctx, of, torch, dist, dev, flush, out)
+    of.ofu_destroy(ctx)
+    return out
+
+
+def e2e(a, g, ctx, of, torch, dist, dev, flush, out):
+    """The same steps through the C ABI from pinned host buffers: the frames
+    go in and every leaf (key, level, u) comes back inside the timed region."""
+    scene = g.scene
+    rule = stop_rule(a, scene)
+    depth_h = torch.from_numpy(scene.depth).pin_memory()
+    intr_h = torch.from_numpy(scene.intr.copy()).pin_memory()
+    pose_h = torch.from_numpy(scene.pose.reshape(-1, 16).copy()).pin_memory()
+    cap = 4 * max(out["leaves_initial"], out["leaves_final"])
+    keys_h = torch.empty(cap, dtype=torch.int64).pin_memory()
+    lev_h = torch.empty(cap, dtype=torch.uint8).pin_memory()
+    u_h = torch.empty(cap, dtype=torch.float32).pin_memory()
+    ts, lis, d2h = [], 0, 0
+    if dist:
+        dist.barrier()
+    for _ in range(a.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        of.ofu_integrate_frames(ctx, g.F, g.H, g.W, depth_h.data_ptr(), intr_h.data_ptr(), pose_h.data_ptr())
+        done, li, e = run_solve(of, ctx, rule)
+        n = of.ofu_export_leaves(ctx, keys_h.data_ptr(), lev_h.data_ptr(), u_h.data_ptr(), cap)
+        ts.append(time.perf_counter() - t0)
+        lis += li
+        d2h = n * (8 + 1 + 4) + 24
+    total, lis = aggregate(dist, sum(ts), lis, dev)
+    return {"value": lis / total, "unit": METRIC,
+            "h2d_bytes_per_step": int(scene.depth.nbytes + scene.intr.nbytes + scene.pose.nbytes),
+            "d2h_bytes_per_step": int(d2h)}
+
+
+def time_to_energy(a, scene, of, torch, dev):
+    """Reference energy E* = the plain float32 solver's primal energy at a
+    relative gap below 1e-5: split/join every R iterations during the
+    workload's refinement iterations (its whole iteration count when it has
+    no gap rule), then on that structure, gap checked every 50 iterations
+    (cap 20000 iterations).  Then, per form, the device time from the frames
+    (construction included) and the iterations until the primal energy
+    first drops to E* (1 + 1e-4), checked after every window of the same
+    schedule."""
+    g = Gpu(scene, of, torch, dev)
+    cap, R, refine, check, tol = stop_rule(a, scene)
+    refine = refine or cap
+    check = check or 50
+    limit = 20000
     from paper_1608_07411_gb300 import warm_start
     try:
-        net = of.ofu_mlp_create(stream.cuda_stream)
+        net = of.ofu_mlp_create(g.stream.cuda_stream)
         of.ofu_mlp_set_params(net, warm_start.load_params())
     except (OSError, ValueError):
         net = None
 
     def ctx_for(fp16, warm=False):
-        c = of.ofu_create_octree(of.params_for(scene, sample_fp16=fp16), stream.cuda_stream)
-        of.ofu_integrate_frames(c, F, H, W, depth_d.data_ptr(), intr_d.data_ptr(), pose_d.data_ptr())
+        c = g.ctx(fp16)
+        g.integrate(c)
         if warm:
             of.ofu_warm_start(c, net)
         return c
 
+    def windows(c, stop):
+        """Runs the schedule window by window until stop(it, energies) or the cap."""
+        it, e = 0, None
+        while it < limit:
+            n = R if it < refine else check
+            _, _, e = of.ofu_solve(c, n, 0, n, 0.0)
+            it += n
+            if stop(it, e):
+                return it, e, True
+            if it < refine:
+                of.ofu_restructure(c)
+        return it, e, False
+
+    traj = []
+
+    def ref_stop(it, e):
+        traj.append([it, e[0], rel_gap(e), of.ofu_num_leaves(c)])
+        return it >= refine and rel_gap(e) < 1e-5
+
     c = ctx_for(False)
-    done, li, (Pr, Dr, Gr) = of.ofu_solve(c, iters, R, 0, 0.0)
+    it, e, conv = windows(c, ref_stop)
     of.ofu_destroy(c)
-    target = Pr * (1 + 1e-4)
-    out = {"reference": f"plain float32 energy after {iters} iterations", "reference_energy": Pr,
-           "reference_gap": Gr, "target": target, "check_every": R}
+    target = e[0] * (1 + 1e-4)
+    step = max(1, len(traj) // 30)
+    out = {"reference": f"plain float32: split/join every {R} iterations for {refine}, then that structure "
+                        f"until the relative gap < 1e-5 (checked every {check})",
+           "reference_iters": it, "reference_energy": e[0], "reference_rel_gap": rel_gap(e),
+           "converged": conv, "target": target,
+           "gap_trajectory": traj[::step] + ([traj[-1]] if (len(traj) - 1) % step else [])}
     forms = [("plain_f32", False, False), ("f16_samples", True, False)]
     if net is not None:
         forms += [("f32_warm_start", False, True), ("f16_warm_start", True, True)]
     for name, fp16, warm in forms:
         torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
+        ev0 = g.event()
         c = ctx_for(fp16, warm)
-        it, reached, P = 0, False, float("inf")
-        while it < 4 * iters:
-            _, _, (P, _, _) = of.ofu_solve(c, R, 0, R, 0.0)
-            it += R
-            if P <= target:
-                reached = True
-                break
-            of.ofu_restructure(c)
-        ev1.record(stream)
+        it, e, reached = windows(c, lambda it, e: e[0] <= target)
+        ev1 = g.event()
         ev1.synchronize()
-        out[name] = {"ms": ev0.elapsed_time(ev1), "iters": it, "reached": reached, "energy": P}
+        out[name] = {"ms": ev0.elapsed_time(ev1), "iters": it, "reached": reached, "energy": e[0]}
         of.ofu_destroy(c)
     if net is not None:
         of.ofu_mlp_destroy(net)
+    return out
+
+
+def _field_err(x, ref):
+    d = np.abs(np.asarray(x, np.float64) - np.asarray(ref, np.float64))
+    return {"max_abs": float(d.max()) if d.size else 0.0, "rms": float(np.sqrt((d * d).mean())) if d.size else 0.0}
+
+
+def precision(a, scene, of, torch, dev, iters=100):
+    """The float16-sample form against float32 and against the FP64 oracle on
+    one fixed structure (no restructuring, so leaves correspond one to one):
+    (1) on the oracle's bounded sample (a node of the scan, built by both
+    sides bit for bit), per-field max-abs and RMS errors of u and p after
+    `iters` iterations of each form against float64; (2) on the whole scan,
+    float16 against float32 and the primal kernel's GB/s of each form."""
+    from oracle import solver
+    out = {"iterations": iters, "fixed_structure": True}
+    crop, st = oracle_crop(scene)
+    solver.step(st, iters)
+    from oracle import tsdf
+    st16 = solver.initial_state(crop)
+    st16.fs = st16.fs.astype(np.float32).astype(np.float16).astype(np.float64)
+    st16.u = tsdf.median(st16.fs, st16.W)   # the float16 form starts from the rounded samples' median
+    st16.ubar = st16.u.copy()
+    solver.step(st16, iters)
+    gc = Gpu(crop, of, torch, dev)
+    for name, fp16 in (("f32", False), ("f16", True)):
+        c = gc.ctx(fp16)
+        gc.integrate(c)
+        keys = np.empty(of.ofu_num_leaves(c), np.uint64)
+        of.ofu_export_leaves(c, keys, None, None, len(keys))
+        assert np.array_equal(keys, st.keys), "crop structure differs from the oracle's"
+        of.ofu_iterate(c, iters)
+        u = np.empty(len(keys), np.float32)
+        p = np.empty(3 * len(keys), np.float32)
+        of.ofu_export_field(c, of.FIELD_U, u, len(u))
+        of.ofu_export_field(c, of.FIELD_P, p, len(p))
+        p = p.reshape(3, -1).T
+        out[f"{name}_vs_fp64_oracle"] = {"u": _field_err(u, st.u), "p": _field_err(p, st.p),
+                                         "leaves": len(keys)}
+        if fp16:
+            out["f16_vs_fp64_oracle_on_f16_rounded_samples"] = {"u": _field_err(u, st16.u),
+                                                                "p": _field_err(p, st16.p)}
+        of.ofu_destroy(c)
+    g = Gpu(scene, of, torch, dev)
+    fields = {}
+    for name, fp16 in (("f32", False), ("f16", True)):
+        c = g.ctx(fp16)
+        g.integrate(c)
+        of.ofu_profile(c, True)
+        of.ofu_iterate(c, iters)
+        ms, nl, ab = of.ofu_profile_read(c)
+        of.ofu_profile(c, False)
+        n = of.ofu_num_leaves(c)
+        u = np.empty(n, np.float32)
+        p = np.empty(3 * n, np.float32)
+        of.ofu_export_field(c, of.FIELD_U, u, n)
+        of.ofu_export_field(c, of.FIELD_P, p, 3 * n)
+        fields[name] = (u, p)
+        out[f"{name}_primal_kernel"] = {"GB_s": ab[1] / (ms[1] * 1e-3) / 1e9, "us": 1e3 * ms[1] / nl[1],
+                                        "alg_bytes_per_launch": ab[1] / nl[1]}
+        out[f"{name}_iteration_us"] = 1e3 * (ms[0] + ms[1]) / nl[0]
+        of.ofu_destroy(c)
+    out["f16_vs_f32_whole_scan"] = {"u": _field_err(fields["f16"][0], fields["f32"][0]),
+                                    "p": _field_err(fields["f16"][1], fields["f32"][1]),
+                                    "leaves": len(fields["f32"][0])}
     return out
 
 
@@ -282,6 +582,23 @@ def aggregate(dist, total_ms, work, device):
     w = torch.tensor([work], dtype=torch.float64, device=device)
     dist.all_reduce(w, op=dist.ReduceOp.SUM)
     return float(t.item()), float(w.item())
+
+
+def roofline(res, workload):
+    ms, nl, ab = res["profile"]["ms"], res["profile"]["launches"], res["profile"]["alg_bytes"]
+    names = ("k_dual", "k_primal")
+    dom = 0 if ms[0] > ms[1] else 1
+    achieved = ab[dom] / (ms[dom] * 1e-3) / 1e9 if ms[dom] > 0 else 0.0
+    peak, kind = peak_hbm()
+    per = ab[dom] / max(nl[dom], 1)
+    traffic = measured_traffic(names[dom], workload, per)
+    o = 1 - dom
+    return {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": kind, "traffic": traffic, "alg_bytes_per_launch": per,
+            "launches": int(nl[dom]), "avg_launch_us": 1e3 * ms[dom] / max(nl[dom], 1),
+            "other": {"kernel": names[o], "achieved": ab[o] / (ms[o] * 1e-3) / 1e9 if ms[o] > 0 else 0.0,
+                      "frac": (ab[o] / (ms[o] * 1e-3) / 1e9) / peak if ms[o] > 0 else 0.0,
+                      "avg_launch_us": 1e3 * ms[o] / max(nl[o], 1)}}
 
 
 def main():
@@ -315,146 +632,63 @@ def main():
     of.load()
 
     scene = make_scene(a.workload, a.seed + rank)
-    iters = a.iters or scene.iters
-    R = scene.restructure_every
     dev = torch.device("cuda", torch.cuda.current_device())
-    stream = torch.cuda.current_stream()
-    depth_d = torch.from_numpy(scene.depth).to(dev)
-    intr_d = torch.from_numpy(scene.intr.copy()).to(dev)
-    pose_d = torch.from_numpy(scene.pose.reshape(-1, 16).copy()).to(dev)
-    F, H, W = scene.depth.shape
-    ctx = of.ofu_create_octree(of.params_for(scene, sample_fp16=a.fp16), stream.cuda_stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-
-    s0s = []
-    cons_ev = []
-
-    def step(timed=False):
-        if timed:
-            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            c0.record(stream)
-        of.ofu_integrate_frames(ctx, F, H, W, depth_d.data_ptr(), intr_d.data_ptr(), pose_d.data_ptr())
-        if timed:
-            c1.record(stream)
-            cons_ev.append((c0, c1))
-        n0 = of.ofu_num_leaves(ctx)
-        s0s.append(of.ofu_export_field(ctx, of.FIELD_SAMPLES, None, 0))
-        done, li, e = of.ofu_solve(ctx, iters, R, 0, 0.0)
-        return n0, li, e
-
-    for _ in range(max(a.warmup, 0)):
-        step()
-    torch.cuda.synchronize()
-
-    # ---- device-timed steps (inputs resident in HBM) ----
     try:
         uuid = str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         uuid = ""
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     clocks = Clocks(uuid)
-    of.ofu_profile(ctx, True)
-    l0 = of.ofu_kernel_launches()
-    times, leaf_iters, n0s, energies = [], 0, [], None
-    for _ in range(a.steps):
-        flush.zero_()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        n0, li, energies = step(timed=True)
-        ev1.record(stream)
-        ev1.synchronize()
-        times.append(ev0.elapsed_time(ev1))
-        leaf_iters += li
-        n0s.append(n0)
-    torch.cuda.synchronize()
-    launches = of.ofu_kernel_launches() - l0
-    ms, nl, ab = of.ofu_profile_read(ctx)
-    of.ofu_profile(ctx, False)
+    res = measure(a, scene, of, torch, dev, flush, dist, a.fp16, with_e2e=True)
     clk = clocks.stop()
-    n_final = of.ofu_num_leaves(ctx)
-    n_samples = of.ofu_export_field(ctx, of.FIELD_SAMPLES, None, 0)
-    total_ms, leaf_iters_all = aggregate(dist, sum(times), leaf_iters, dev)
-    value = leaf_iters_all / (total_ms / 1e3)
 
-    # ---- end to end through the C ABI with pinned host buffers ----
-    depth_h = torch.from_numpy(scene.depth).pin_memory()
-    intr_h = torch.from_numpy(scene.intr.copy()).pin_memory()
-    pose_h = torch.from_numpy(scene.pose.reshape(-1, 16).copy()).pin_memory()
-    cap = 4 * max(n0s + [n_final])
-    keys_h = torch.empty(cap, dtype=torch.int64).pin_memory()
-    lev_h = torch.empty(cap, dtype=torch.uint8).pin_memory()
-    u_h = torch.empty(cap, dtype=torch.float32).pin_memory()
-    e2e_t, e2e_li, d2h = [], 0, 0
-    if dist:
-        dist.barrier()
-    for _ in range(a.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        of.ofu_integrate_frames(ctx, F, H, W, depth_h.data_ptr(), intr_h.data_ptr(), pose_h.data_ptr())
-        done, li, e = of.ofu_solve(ctx, iters, R, 0, 0.0)
-        n = of.ofu_export_leaves(ctx, keys_h.data_ptr(), lev_h.data_ptr(), u_h.data_ptr(), cap)
-        e2e_t.append(time.perf_counter() - t0)
-        e2e_li += li
-        d2h = n * (8 + 1 + 4) + 24
-    e2e_total, e2e_li = aggregate(dist, sum(e2e_t), e2e_li, dev)
-    e2e_val = e2e_li / e2e_total
-    h2d = scene.depth.nbytes + scene.intr.nbytes + scene.pose.nbytes
+    second = None
+    sec_scene = None
+    if a.second not in ("none", a.workload):
+        sec_scene = make_scene(a.second, a.seed + rank)
+        r2 = measure(a, sec_scene, of, torch, dev, flush, dist, a.fp16, with_e2e=False)
+        second = {"workload": f"{sec_scene.name}: {WORKLOAD_TEXT[sec_scene.name]}", "value": r2["value"],
+                  "unit": METRIC, "ms_per_step": r2["ms_per_step"], "iterations": r2["iterations"],
+                  "leaves_initial": r2["leaves_initial"], "leaves_final": r2["leaves_final"],
+                  "samples_initial": r2["samples_initial"], "iterate_only": r2["iterate_only"],
+                  "roofline": roofline(r2, sec_scene.name), "construction": r2["construction"]}
 
-    # ---- roofline of the dominant iteration kernel ----
-    names = ("k_dual", "k_primal")
-    dom = 0 if ms[0] > ms[1] else 1
-    achieved = ab[dom] / (ms[dom] * 1e-3) / 1e9 if ms[dom] > 0 else 0.0
-    peak, peak_kind = peak_hbm()
-    alg_per_launch = ab[dom] / max(nl[dom], 1)
-    traffic = measured_traffic(names[dom], alg_per_launch)
-    roof = {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
-            "alg_bytes_per_launch": alg_per_launch, "launches": int(nl[dom]),
-            "avg_launch_us": 1e3 * ms[dom] / max(nl[dom], 1),
-            "other": {"kernel": names[1 - dom], "achieved": (ab[1 - dom] / (ms[1 - dom] * 1e-3) / 1e9)
-                      if ms[1 - dom] > 0 else 0.0, "avg_launch_us": 1e3 * ms[1 - dom] / max(nl[1 - dom], 1)},
-            "iteration_share_of_step": (ms[0] + ms[1]) / sum(times)}
-
-    # iteration kernels alone, and the construction (Eq. 1 at every finest voxel for the
-    # median field, then count and fill passes over the leaves) on its own
-    iterate_only = {"value": leaf_iters / ((ms[0] + ms[1]) * 1e-3) if ms[0] + ms[1] > 0 else 0.0,
-                    "unit": METRIC, "kernels": list(names), "scope": "rank 0"}
-    cons_ms = statistics.median(c0.elapsed_time(c1) for c0, c1 in cons_ev)
-    evals = (8 ** scene.max_depth + 2 * int(statistics.median(n0s))) * F
-    construction = {"ms": cons_ms, "eq1_evaluations": evals,
-                    "eq1_evaluations_per_s": evals / (cons_ms * 1e-3), "finest_voxels": 8 ** scene.max_depth,
-                    "frames": F, "share_of_step": cons_ms * a.steps / sum(times)}
-
-    tte = None if a.no_tte else time_to_energy(a, scene, of, stream, depth_d, intr_d, pose_d)
+    tte = None if a.no_tte or rank != 0 else time_to_energy(a, scene, of, torch, dev)
+    prec = None
+    if not a.no_precision and rank == 0:
+        pscene = sec_scene if sec_scene is not None and sec_scene.name == "torus_box" else \
+            make_scene("torus_box", a.seed)
+        prec = precision(a, pscene, of, torch, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        rate, nleaf, it, dt, setup = cpu_rate(scene, a.cpu_seconds)
-        cpu = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
-               "sample": f"float64 NumPy/SciPy oracle, single thread: {it} iterations on the {nleaf} "
-                         f"leaves of the level-2 node around {CROP_POINT[scene.name]} ({dt:.1f} s timed, "
-                         f"{setup:.1f} s construction untimed)"}
+        r = cpu_rate(scene, a.cpu_seconds)
+        pt, sub = CROP[scene.name]
+        val, cores = (r["all_cores"], r["cores"]) if r["all_cores"] else (r["one_core"], 1)
+        cpu = {"value": val, "unit": METRIC, "cores": cores, "kind": "oracle",
+               "one_core": r["one_core"], "host_cores": r["cores"], "cpu_model": cpu_model(),
+               "sample": f"float64 NumPy/SciPy oracle on the {r['leaves']} leaves of the level-{sub} node "
+                         f"around {pt} (its own construction, {r['setup_s']:.1f} s, untimed): "
+                         f"{r['seconds']:.0f} s of iterations in one process, then the same in "
+                         f"{r['cores']} independent processes at once (value = their sum)"}
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "metric": METRIC, "value": res["value"], "unit": METRIC, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16-samples/f32" if a.fp16 else "f32",
             "data": "synthetic", "config": config_of(a, scene, extra={
-                "leaves_initial": int(statistics.median(n0s)), "leaves_final": n_final,
-                "samples_initial": int(statistics.median(s0s)),
-                "samples_final": n_samples, "final_energy": energies}),
-            "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": int(launches),
-            "roofline": roof, "clocks": clk, "cpu_baseline": cpu, "time_to_energy": tte,
-            "iterate_only": iterate_only, "construction": construction,
+                "leaves_initial": res["leaves_initial"], "leaves_final": res["leaves_final"],
+                "samples_initial": res["samples_initial"], "samples_final": res["samples_final"]}),
+            "solve": {"iterations": res["iterations"], "rel_gap": res["rel_gap"], "gap_tol": res["gap_tol"],
+                      "gap_reached": res["gap_reached"], "final_energy": res["final_energy"],
+                      "leaf_iterations_per_step": res["leaf_iterations_per_step"]},
+            "e2e": res["e2e"], "gpu_launches": int(res["gpu_launches"]),
+            "roofline": roofline(res, scene.name), "clocks": clk, "cpu_baseline": cpu,
+            "iterate_only": res["iterate_only"], "construction": res["construction"],
+            "time_to_energy": tte, "precision": prec, "second_workload": second,
         }
         print(json.dumps(line), flush=True)
-    of.ofu_destroy(ctx)
     if dist:
         dist.barrier()
         dist.destroy_process_group()

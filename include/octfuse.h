@@ -80,11 +80,15 @@ typedef struct {
   double tau_join;     /* join a subtree when all |u| > tau_join (>= tau_split) */
   double spread_tau;   /* Eq. 2 construction threshold (the paper uses 0.1) */
   int64_t max_leaves;  /* hard cap on the leaf count (0 = 2^27, the maximum) */
+  int32_t data_term;   /* source of each leaf's frame samples: 0 = Eq. 1 at the leaf
+                          centre; 1 = the per-frame TSDF octrees of Sec. 3.1 read by
+                          the Fig. 4 rule (see ofu_integrate_frames) */
+  int32_t reserved;    /* 0 */
 } ofu_params;
 
 /* Fills `p` with the defaults: origin (-0.5,-0.5,-0.5), extent 1, max_depth 6,
  * float32 samples, delta 4 voxels, eta 2 delta, lambda 0.5, gamma 1e-3,
- * tau_split 0.95, tau_join 0.99, spread_tau 0.1, max_leaves 0. */
+ * tau_split 0.95, tau_join 0.99, spread_tau 0.1, max_leaves 0, data_term 0. */
 void ofu_default_params(ofu_params* p);
 
 /* Creates an empty context on the current CUDA device.  `cuda_stream` is a
@@ -208,6 +212,62 @@ ofu_status ofu_descend(ofu_ctx* ctx, int32_t n, int32_t t0, double eps, double x
  * sums; the terms are summed in a fixed order.  Synchronises.  EINVAL for
  * NULL pointers or a wrong n_fine; ESTATE before ofu_integrate_frames. */
 ofu_status ofu_quantisation_error(ofu_ctx* ctx, const float* fine, int64_t n_fine, double* err);
+
+/* ---- per-frame TSDF octrees (data_term = 1) ------------------------------
+ *
+ * With data_term = 1, ofu_integrate_frames (and ofu_load) also turns each
+ * frame's TSDF into an octree f_i* (Sec. 3.1, "Octree construction"): Eq. 1
+ * at every finest-voxel centre for that frame alone, then top-down, a node is
+ * split while its voxels do not all share one weight, or while all are
+ * observed and the spread of f over them exceeds spread_tau (Eq. 2); every
+ * node holds the mean of the observed f below it and weight 1 when any voxel
+ * below it is observed.  A leaf of the iterate at level L then takes, from
+ * each frame, the deepest node of that frame's tree on its path at a level
+ * <= L (Fig. 4: the node at the leaf's level, else the tree leaf containing
+ * it) as its sample, unobserved when that node's weight is 0; this replaces
+ * Eq. 1 at the leaf centre for every sample (construction's median field
+ * still uses Eq. 1 at the finest voxels).  Means are float64 quotients of
+ * float64 sums, stored as float32 (or float16) samples. */
+
+/* Leaves of frame `frame`'s tree, sorted by Morton key (keys uint64,
+ * levels uint8; host or device; NULL to size).  *n receives the count;
+ * ECAPACITY when cap is too small; ESTATE without data_term = 1 frames.
+ * Synchronises. */
+ofu_status ofu_export_frame_tree(ofu_ctx* ctx, int32_t frame, uint64_t* keys, uint8_t* levels,
+                                 int64_t cap, int64_t* n);
+
+/* Memory of the data term, Table 1's comparison: dense_bytes = frames x
+ * 8^max_depth voxels x (a float distance + a float weight); octree_bytes =
+ * nodes of all frame trees x (9 pointers + 3 floats, the node layout of
+ * Sec. 4.1); device_bytes = what this library keeps on the device for the
+ * trees; nodes (int64 [frames], host, may be NULL) per frame.  Any output
+ * may be NULL.  ESTATE without data_term = 1 frames. */
+ofu_status ofu_data_term_memory(ofu_ctx* ctx, int64_t* nodes, int64_t* dense_bytes,
+                                int64_t* octree_bytes, int64_t* device_bytes);
+
+/* Zero level set of the current field as a triangle mesh (Sec. 3.3: the
+ * fused result is meshed by marching cubes).  The field is sampled at every
+ * finest-voxel centre (each voxel takes its leaf's u); cubes have eight
+ * neighbouring centres as corners; u < 0 is inside.  One vertex per grid edge
+ * whose ends differ in sign, at t = a / (a - b) from the edge's lower end
+ * (float64, then stored as float32 world coordinates origin + (i + 1/2 +
+ * t e) * extent / 2^max_depth); vertices are shared between cubes.  Each
+ * cube's triangles follow from its faces (no case table): on each face, seen
+ * from outside with corners counter-clockwise, a contour segment starts at
+ * every crossing where the walk goes from outside to inside and ends at the
+ * walk's next crossing; the segments close into loops, taken in the order
+ * found (faces -x, +x, -y, +y, -z, +z) and fanned from their first vertex, so
+ * triangle normals point outside (u >= 0) and the mesh is closed.
+ *
+ * Output order: vertices by voxel (x-major index (x n + y) n + z, n =
+ * 2^max_depth) then axis; triangles by cube (the same index of its lowest
+ * voxel), then loop, then fan.  verts: float32 [V][3], tris: int32 [T][3]
+ * (host or device; either may be NULL); *n_verts and *n_tris receive V and T
+ * (call with NULL buffers to size them).  ECAPACITY, nothing written, when a
+ * given buffer is smaller than the mesh.  Scratch: about 13 bytes per finest
+ * voxel, kept by the context.  Synchronises. */
+ofu_status ofu_extract_mesh(ofu_ctx* ctx, float* verts, int64_t vcap, int32_t* tris, int64_t tcap,
+                            int64_t* n_verts, int64_t* n_tris);
 
 /* ---- inspection and test hooks ----------------------------------------- */
 
@@ -366,11 +426,13 @@ ofu_status ofu_energy_static(ofu_ctx* ctx, double* out3);
 /* Number of CUDA kernels this library has launched in this process. */
 int64_t ofu_kernel_launches(void);
 
-/* enable = 1 clears and starts per-launch timing of the two iteration kernels
- * (dual step, primal step) with CUDA events recorded on the context's stream
- * around each launch made by ofu_iterate / ofu_solve; enable = 0 stops it.
- * The first enable creates a pool of events for 8192 iterations (outside any
- * timed work); iterations beyond that are not timed until the next enable. */
+/* enable >= 1 clears and starts per-launch timing of the two iteration
+ * kernels (dual step, primal step) with CUDA events recorded on the context's
+ * stream around each launch made by ofu_iterate / ofu_solve; enable = 0 stops
+ * it.  The event pool is created here (outside any timed work) for
+ * max(enable, 8192) iterations and kept; iterations beyond the pool are not
+ * timed (and not counted by ofu_profile_read) until the next enable.  EINVAL
+ * for enable < 0 or > 2^20. */
 ofu_status ofu_profile(ofu_ctx* ctx, int32_t enable);
 
 /* Reads the timing since ofu_profile(ctx, 1) (synchronises): per kernel

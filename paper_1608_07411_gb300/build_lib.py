@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libofu.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ("api.cu", "build.cu", "solve.cu", "mlp.cu", "descent.cu", "quant.cu")
+SOURCES = ("api.cu", "build.cu", "solve.cu", "mlp.cu", "descent.cu", "quant.cu", "mesh.cu",
+           "frames.cu")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -8,6 +8,8 @@
 #include <vector>
 
 #include "descent.cuh"
+#include "frames.cuh"
+#include "mesh.cuh"
 #include "ofu_internal.cuh"
 #include "quant.cuh"
 
@@ -29,7 +31,7 @@ thread_local std::string g_create_error;
 enum Buf {
   B_SCAN, B_U0, B_PYR, B_FLAGS, B_POS, B_CNT, B_OVFC, B_CLS, B_OUTC, B_JL, B_SRC, B_LIST,
   B_SMALL, B_PART, B_BIG, B_LONGQ, B_FWD, B_AUX, B_FULL, B_PENDQ, B_Q, B_QF, B_QD, B_QT, B_LFL,
-  B_NUM
+  B_MG, B_MC, B_MN, B_MV, B_MT, B_FTC, B_FTT, B_FTL, B_FTH, B_NUM
 };
 
 struct Bufs {
@@ -203,11 +205,127 @@ ofu_status read_back(ofu_ctx* ctx, const void* dev, size_t bytes, void* host) {
   return OFU_OK;
 }
 
-// Events of the per-launch timing (3 per iteration: 8192 iterations).
+// Events of the per-launch timing: 3 per iteration, at least 8192 iterations;
+// at most 2^20 iterations.
 constexpr size_t kProfEvents = 3 * 8192;
+constexpr int32_t kProfMaxIters = 1 << 20;
 
 int64_t max_leaves(const ofu_ctx* ctx) {
   return ctx->prm.max_leaves > 0 ? std::min<int64_t>(ctx->prm.max_leaves, kMaxLeaves) : kMaxLeaves;
+}
+
+// The per-frame trees handed to the sample kernels (empty: Eq. 1 at centres).
+FrameTrees trees_of(const ofu_ctx* ctx) {
+  FrameTrees t;
+  if (ctx->prm.data_term == 1 && ctx->ft_start) {
+    t.start = ctx->ft_start;
+    t.key = ctx->ft_key;
+    t.level = ctx->ft_level;
+    t.cnt = ctx->ft_cnt;
+    t.tot = ctx->ft_tot;
+    t.pcnt = ctx->ft_pcnt;
+    t.ptot = ctx->ft_ptot;
+  }
+  return t;
+}
+
+void free_frame_trees(ofu_ctx* ctx) {
+  for (void* q : {static_cast<void*>(ctx->ft_start), static_cast<void*>(ctx->ft_key),
+                  static_cast<void*>(ctx->ft_level), static_cast<void*>(ctx->ft_cnt),
+                  static_cast<void*>(ctx->ft_tot), static_cast<void*>(ctx->ft_pcnt),
+                  static_cast<void*>(ctx->ft_ptot)})
+    dfree(ctx, q);
+  ctx->ft_start = nullptr;
+  ctx->ft_key = nullptr;
+  ctx->ft_level = nullptr;
+  ctx->ft_cnt = nullptr;
+  ctx->ft_tot = nullptr;
+  ctx->ft_pcnt = nullptr;
+  ctx->ft_ptot = nullptr;
+  ctx->ft_cap = 0;
+  ctx->ft_host_start.clear();
+}
+
+// Grows the tree-leaf arrays to hold `need` leaves, keeping the first `keep`.
+ofu_status grow_frame_trees(ofu_ctx* ctx, int64_t need, int64_t keep) {
+  if (need <= ctx->ft_cap) return OFU_OK;
+  const int64_t cap = std::max<int64_t>(need + need / 2, 1 << 16);
+  uint64_t *key, *cnt;
+  uint8_t* level;
+  double* tot;
+  CU(dalloc(ctx, &key, size_t(cap) * 8));
+  CU(dalloc(ctx, &level, size_t(cap)));
+  CU(dalloc(ctx, &cnt, size_t(cap) * 8));
+  CU(dalloc(ctx, &tot, size_t(cap) * 8));
+  if (keep > 0) {
+    CU(cudaMemcpyAsync(key, ctx->ft_key, size_t(keep) * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(level, ctx->ft_level, size_t(keep), cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(cnt, ctx->ft_cnt, size_t(keep) * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(tot, ctx->ft_tot, size_t(keep) * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  for (void* q : {static_cast<void*>(ctx->ft_key), static_cast<void*>(ctx->ft_level),
+                  static_cast<void*>(ctx->ft_cnt), static_cast<void*>(ctx->ft_tot)})
+    CU(dfree(ctx, q));
+  ctx->ft_key = key;
+  ctx->ft_level = level;
+  ctx->ft_cnt = cnt;
+  ctx->ft_tot = tot;
+  ctx->ft_cap = cap;
+  return OFU_OK;
+}
+
+// Per-frame TSDF octrees of the current frames (data_term = 1), frame by
+// frame: pyramid and leaf flags, scan, one read-back of the frame's leaf
+// count, emission; then prefix sums of counts and sums over all frames.
+ofu_status build_frame_trees(ofu_ctx* ctx) {
+  const int D = ctx->prm.max_depth;
+  const int64_t nvox = int64_t(1) << (3 * D);
+  const size_t npyr = frame_pyramid_nodes(D);
+  uint32_t *pc, *flags, *pos, *tmp;
+  double* pt;
+  float *pl, *ph;
+  ST(ensure(ctx, B_FTC, std::max<size_t>(npyr, 1), &pc));
+  ST(ensure(ctx, B_FTT, std::max<size_t>(npyr, 1), &pt));
+  ST(ensure(ctx, B_FTL, std::max<size_t>(npyr, 1), &pl));
+  ST(ensure(ctx, B_FTH, std::max<size_t>(npyr, 1), &ph));
+  ST(ensure(ctx, B_FLAGS, size_t(nvox), &flags));
+  ST(ensure(ctx, B_POS, size_t(nvox + 1), &pos));
+  ST(ensure(ctx, B_SCAN, scan_tmp_items<uint32_t>(nvox) * 2, &tmp));
+  const Geo g = geo_of(ctx);
+  std::vector<int64_t> start(size_t(ctx->F) + 1, 0);
+  for (int i = 0; i < ctx->F; ++i) {
+    const float* range = ctx->depth + size_t(i) * ctx->H * ctx->W;
+    CU(launch_frame_tree_flags(range, ctx->cams + i, ctx->H, ctx->W, g, ctx->prm.spread_tau, pc, pt,
+                               pl, ph, flags, ctx->stream));
+    CU(scan_exclusive<uint32_t>(flags, pos, nvox, tmp, ctx->stream));
+    uint32_t ni = 0;
+    ST(read_back(ctx, pos + nvox, sizeof(uint32_t), &ni));
+    ST(grow_frame_trees(ctx, start[i] + int64_t(ni), start[i]));
+    const int64_t o = start[i];
+    CU(launch_frame_tree_emit(flags, pos, pc, pt, pl, ph, ctx->prm.spread_tau, range, ctx->cams + i,
+                              ctx->H, ctx->W, g, ctx->ft_key + o, ctx->ft_level + o, ctx->ft_cnt + o,
+                              ctx->ft_tot + o, ctx->stream));
+    start[i + 1] = o + int64_t(ni);
+  }
+  const int64_t total = start[ctx->F];
+  for (void* q : {static_cast<void*>(ctx->ft_start), static_cast<void*>(ctx->ft_pcnt),
+                  static_cast<void*>(ctx->ft_ptot)})
+    CU(dfree(ctx, q));
+  ctx->ft_start = nullptr;
+  ctx->ft_pcnt = nullptr;
+  ctx->ft_ptot = nullptr;
+  CU(dalloc(ctx, &ctx->ft_start, start.size() * 8));
+  CU(dalloc(ctx, &ctx->ft_pcnt, size_t(total + 1) * 8));
+  CU(dalloc(ctx, &ctx->ft_ptot, size_t(total + 1) * 8));
+  CU(cudaMemcpyAsync(ctx->ft_start, start.data(), start.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+  uint64_t* t64;
+  ST(ensure(ctx, B_OUTC, scan_tmp_items<uint64_t>(total) * 2 + scan_tmp_items<double>(total) * 2, &t64));
+  CU(scan_exclusive<uint64_t>(ctx->ft_cnt, ctx->ft_pcnt, total, t64, ctx->stream));
+  CU(scan_exclusive<double>(ctx->ft_tot, ctx->ft_ptot, total, reinterpret_cast<double*>(t64),
+                            ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));   // the host copy of start is released on return
+  ctx->ft_host_start = start;
+  return OFU_OK;
 }
 
 // Voxel -> leaf map of the current structure.
@@ -308,14 +426,14 @@ ofu_status integrate_all(ofu_ctx* ctx, bool init) {
   uint32_t* tmp;
   ST(ensure(ctx, B_SCAN, scan_tmp_items<uint32_t>(n) * 2, &tmp));
   CU(launch_leaf_count(L.key, L.level, nullptr, nullptr, n, ctx->depth, ctx->cams, ctx->F, ctx->H,
-                       ctx->W, g, L.soff, ctx->stream));
+                       ctx->W, g, trees_of(ctx), L.soff, ctx->stream));
   CU(scan_exclusive<uint32_t>(L.soff, L.soff, n, tmp, ctx->stream));
   uint32_t total = 0;
   ST(read_back(ctx, L.soff + n, sizeof(uint32_t), &total));
   ST(ensure_samples(ctx, ctx->cur, int64_t(total)));
   ctx->n_samples = total;
   CU(launch_leaf_fill(L.key, L.level, nullptr, nullptr, n, ctx->depth, ctx->cams, ctx->F, ctx->H,
-                      ctx->W, g, L.soff, ctx->samp[ctx->cur], ctx->prm.sample_fp16 != 0,
+                      ctx->W, g, trees_of(ctx), L.soff, ctx->samp[ctx->cur], ctx->prm.sample_fp16 != 0,
                       init ? L.u : nullptr, init ? L.ubar : nullptr, ctx->stream));
   if (init) CU(cudaMemsetAsync(L.p, 0, 3 * L.cap * sizeof(float), ctx->stream));
   return OFU_OK;
@@ -352,6 +470,8 @@ ofu_status validate(const ofu_params* p, std::string* why) {
   if (p->tau_join < p->tau_split) return bad("tau_join must be >= tau_split");
   if (p->sample_fp16 != 0 && p->sample_fp16 != 1) return bad("sample_fp16 must be 0 or 1");
   if (p->max_leaves < 0) return bad("max_leaves must be >= 0");
+  if (p->data_term != 0 && p->data_term != 1) return bad("data_term must be 0 or 1");
+  if (p->reserved != 0) return bad("reserved must be 0");
   return OFU_OK;
 }
 
@@ -427,6 +547,7 @@ void ofu_destroy(ofu_ctx* ctx) {
   dfree(ctx, ctx->cams);
   dfree(ctx, ctx->map);
   dfree(ctx, ctx->heavy);
+  free_frame_trees(ctx);
   if (ctx->scratch) {
     Bufs& B = bufs(ctx);
     for (int b = 0; b < B_NUM; ++b) dfree(ctx, B.p[b]);
@@ -487,6 +608,7 @@ ofu_status ofu_integrate_frames(ofu_ctx* ctx, int32_t F, int32_t H, int32_t W, c
   ctx->W = W;
   ctx->have_frames = true;
   ctx->n = 0;
+  if (ctx->prm.data_term == 1) ST(build_frame_trees(ctx));
 
   // Eq. 2 construction on the median field
   const Geo g = geo_of(ctx);
@@ -609,14 +731,14 @@ ofu_status ofu_restructure(ofu_ctx* ctx, int64_t* n_split, int64_t* n_join, int6
   CU(launch_kept_counts(src, L.soff, n_new, N2.soff, ctx->stream));
   const Geo g = geo_of(ctx);
   CU(launch_leaf_count(N2.key, N2.level, list, nlist, n_new, ctx->depth, ctx->cams, ctx->F, ctx->H,
-                       ctx->W, g, N2.soff, ctx->stream));
+                       ctx->W, g, trees_of(ctx), N2.soff, ctx->stream));
   CU(scan_exclusive<uint32_t>(N2.soff, N2.soff, n_new, tmp32, ctx->stream));
   ST(ensure_samples(ctx, nx, n_new * int64_t(ctx->F)));
   const bool h16 = ctx->prm.sample_fp16 != 0;
   CU(launch_copy_kept_samples(src, n_new, L.soff, ctx->samp[ctx->cur], N2.soff, ctx->samp[nx], h16,
                               ctx->stream));
   CU(launch_leaf_fill(N2.key, N2.level, list, nlist, n_new, ctx->depth, ctx->cams, ctx->F, ctx->H,
-                      ctx->W, g, N2.soff, ctx->samp[nx], h16, nullptr, nullptr, ctx->stream));
+                      ctx->W, g, trees_of(ctx), N2.soff, ctx->samp[nx], h16, nullptr, nullptr, ctx->stream));
   Carry carry;
   carry.nbr = L.nbr;
   carry.ovf = L.ovf;
@@ -671,6 +793,79 @@ ofu_status ofu_quantisation_error(ofu_ctx* ctx, const float* fine, int64_t n_fin
   CU(cudaMemcpyAsync(f, fine, size_t(nf) * sizeof(float), cudaMemcpyDefault, ctx->stream));
   CU(launch_quant_error(view_of(ctx), ctx->L[ctx->cur].u, f, cfine, terms, tmp, ctx->stream));
   ST(read_back(ctx, terms + ctx->n, sizeof(double), err));
+  return OFU_OK;
+}
+
+ofu_status ofu_export_frame_tree(ofu_ctx* ctx, int32_t frame, uint64_t* keys, uint8_t* levels,
+                                 int64_t cap, int64_t* n) {
+  ST(check_ready(ctx));
+  if (ctx->prm.data_term != 1 || ctx->ft_host_start.empty())
+    return fail(ctx, OFU_ESTATE, "export_frame_tree: no per-frame trees (data_term 1 and frames needed)");
+  if (frame < 0 || frame >= ctx->F) return fail(ctx, OFU_EINVAL, "export_frame_tree: frame out of range");
+  const int64_t o = ctx->ft_host_start[frame], m = ctx->ft_host_start[frame + 1] - o;
+  if (n) *n = m;
+  if (!keys && !levels) return OFU_OK;
+  if (cap < m) return fail(ctx, OFU_ECAPACITY, "export_frame_tree: capacity smaller than the tree");
+  if (keys) CU(cudaMemcpyAsync(keys, ctx->ft_key + o, size_t(m) * 8, cudaMemcpyDefault, ctx->stream));
+  if (levels) CU(cudaMemcpyAsync(levels, ctx->ft_level + o, size_t(m), cudaMemcpyDefault, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return OFU_OK;
+}
+
+ofu_status ofu_data_term_memory(ofu_ctx* ctx, int64_t* nodes, int64_t* dense_bytes,
+                                int64_t* octree_bytes, int64_t* device_bytes) {
+  ST(check_ready(ctx));
+  if (ctx->prm.data_term != 1 || ctx->ft_host_start.empty())
+    return fail(ctx, OFU_ESTATE, "data_term_memory: no per-frame trees (data_term 1 and frames needed)");
+  // a tree with m leaves has (m - 1) / 7 inner nodes (every split adds 8 children)
+  int64_t all = 0;
+  for (int i = 0; i < ctx->F; ++i) {
+    const int64_t m = ctx->ft_host_start[i + 1] - ctx->ft_host_start[i];
+    const int64_t k = m + (m - 1) / 7;
+    if (nodes) nodes[i] = k;
+    all += k;
+  }
+  const int64_t total = ctx->ft_host_start[ctx->F];
+  if (dense_bytes) *dense_bytes = int64_t(ctx->F) * (int64_t(1) << (3 * ctx->prm.max_depth)) * 8;
+  if (octree_bytes) *octree_bytes = all * (9 * 8 + 3 * 4);
+  if (device_bytes) *device_bytes = total * (8 + 1 + 8 + 8) + (total + 1) * 16 + (int64_t(ctx->F) + 1) * 8;
+  return OFU_OK;
+}
+
+ofu_status ofu_extract_mesh(ofu_ctx* ctx, float* verts, int64_t vcap, int32_t* tris, int64_t tcap,
+                            int64_t* n_verts, int64_t* n_tris) {
+  ST(check_built(ctx));
+  const int D = ctx->prm.max_depth;
+  const int64_t nvox = int64_t(1) << (3 * D);
+  float* grid;
+  uint8_t* cm;
+  uint64_t *cnt, *tmp;
+  ST(ensure(ctx, B_MG, size_t(nvox), &grid));
+  ST(ensure(ctx, B_MC, size_t(nvox), &cm));
+  ST(ensure(ctx, B_MN, size_t(nvox + 1), &cnt));
+  ST(ensure(ctx, B_SCAN, scan_tmp_items<uint64_t>(nvox) * 2, &tmp));
+  Leaves& L = ctx->L[ctx->cur];
+  CU(launch_mesh_count(view_of(ctx), L.u, grid, cm, cnt, ctx->stream));
+  CU(scan_exclusive<uint64_t>(cnt, cnt, nvox, tmp, ctx->stream));
+  uint64_t tot = 0;
+  ST(read_back(ctx, cnt + nvox, sizeof(uint64_t), &tot));
+  const int64_t V = int64_t(tot & 0xffffffffu), T = int64_t(tot >> 32);
+  if (n_verts) *n_verts = V;
+  if (n_tris) *n_tris = T;
+  if (!verts && !tris) return OFU_OK;
+  if ((verts && vcap < V) || (tris && tcap < T))
+    return fail(ctx, OFU_ECAPACITY, "extract_mesh: capacity smaller than the mesh (" + std::to_string(V) +
+                                        " vertices, " + std::to_string(T) + " triangles)");
+  if (V >= (int64_t(1) << 31)) return fail(ctx, OFU_ECAPACITY, "extract_mesh: more than 2^31 vertices");
+  float* dv;
+  int32_t* dt;
+  ST(ensure(ctx, B_MV, size_t(3 * V + 3), &dv));
+  ST(ensure(ctx, B_MT, size_t(3 * T + 3), &dt));
+  const double spacing = ctx->prm.extent / double(int64_t(1) << D);
+  CU(launch_mesh_emit(D, grid, cm, cnt, ctx->prm.origin, spacing, dv, dt, ctx->stream));
+  if (verts && V) CU(cudaMemcpyAsync(verts, dv, size_t(3 * V) * sizeof(float), cudaMemcpyDefault, ctx->stream));
+  if (tris && T) CU(cudaMemcpyAsync(tris, dt, size_t(3 * T) * sizeof(int32_t), cudaMemcpyDefault, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
   return OFU_OK;
 }
 
@@ -1189,6 +1384,8 @@ ofu_status ofu_load(ofu_ctx* ctx, const char* path) {
   ctx->W = dims[2];
   ctx->have_frames = true;
   ctx->n = 0;
+  free_frame_trees(ctx);
+  if (ctx->prm.data_term == 1) ST(build_frame_trees(ctx));
   ST(ofu_import_leaves(ctx, keys.data(), lv.data(), n, u.data(), p.data()));
   Leaves& L = ctx->L[ctx->cur];
   CU(cudaMemcpyAsync(L.ubar, ub.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream));
@@ -1200,8 +1397,11 @@ int64_t ofu_kernel_launches(void) { return launches_so_far(); }
 
 ofu_status ofu_profile(ofu_ctx* ctx, int32_t enable) {
   ST(check_ready(ctx));
-  // the event pool is created here, outside any timed work, once per context
-  while (enable && ctx->prof_ev.size() < kProfEvents) {
+  // the event pool is created here, outside any timed work, and only grows
+  if (enable < 0 || enable > kProfMaxIters)
+    return fail(ctx, OFU_EINVAL, "profile: enable must be 0, 1 or an iteration count <= 2^20");
+  const size_t want = std::max(kProfEvents, 3 * size_t(enable));
+  while (enable && ctx->prof_ev.size() < want) {
     cudaEvent_t e;
     CU(cudaEventCreate(&e));
     ctx->prof_ev.push_back(e);

@@ -191,11 +191,10 @@ __device__ __forceinline__ void stage_cams(Cam* sc, const Cam* cams, int F) {
 }
 
 // Samples of one point by one warp into a[0..P) (+inf where unobserved);
-// returns W and the min / max of the observed samples.
-template <int P>
-__device__ __forceinline__ int warp_samples(const Cam* sc, const float* depth, int F, int H, int W,
-                                            float x, float y, float z, float delta, float eta,
-                                            float* a, float* mn, float* mx) {
+// sample(i, &f) gives frame i's sample and whether it is observed.  Returns W
+// and the min / max of the observed samples.
+template <int P, typename Src>
+__device__ __forceinline__ int warp_samples_of(Src sample, int F, float* a, float* mn, float* mx) {
   const int lane = lane_id();
   int cnt = 0;
   float lo = CUDART_INF_F, hi = -CUDART_INF_F;
@@ -204,7 +203,7 @@ __device__ __forceinline__ int warp_samples(const Cam* sc, const float* depth, i
     float f = CUDART_INF_F;
     if (i < F) {
       float t;
-      if (eq1_sample(sc[i], depth + size_t(i) * H * W, H, W, x, y, z, delta, eta, &t)) {
+      if (sample(i, &t)) {
         f = t;
         ++cnt;
         lo = fminf(lo, t);
@@ -216,6 +215,18 @@ __device__ __forceinline__ int warp_samples(const Cam* sc, const float* depth, i
   *mn = warp_min_f(lo);
   *mx = warp_max_f(hi);
   return warp_sum_i(cnt);
+}
+
+// Eq. 1 samples of the point (x, y, z) by one warp (see warp_samples_of).
+template <int P>
+__device__ __forceinline__ int warp_samples(const Cam* sc, const float* depth, int F, int H, int W,
+                                            float x, float y, float z, float delta, float eta,
+                                            float* a, float* mn, float* mx) {
+  return warp_samples_of<P>(
+      [&](int i, float* t) {
+        return eq1_sample(sc[i], depth + size_t(i) * H * W, H, W, x, y, z, delta, eta, t);
+      },
+      F, a, mn, mx);
 }
 
 // Median field, first pass: a thread per finest voxel walks all frames and
@@ -404,7 +415,8 @@ __global__ void __launch_bounds__(256) k_leaf_count(const uint64_t* __restrict__
                                                     int64_t n,
                                                     const float* __restrict__ depth,
                                                     const Cam* __restrict__ cams, int F, int H,
-                                                    int W, Geo g, uint32_t* __restrict__ count) {
+                                                    int W, Geo g, FrameTrees tr,
+                                                    uint32_t* __restrict__ count) {
   extern __shared__ float4 smem_dyn[];
   Cam* sc = reinterpret_cast<Cam*>(smem_dyn);
   stage_cams(sc, cams, F);
@@ -413,12 +425,15 @@ __global__ void __launch_bounds__(256) k_leaf_count(const uint64_t* __restrict__
   for (int64_t j = int64_t(blockIdx.x) * kWarpsPerBlock + warp; j < n;
        j += int64_t(gridDim.x) * kWarpsPerBlock) {
     const int64_t l = list ? int64_t(list[j]) : j;
+    const uint64_t kl = key[l];
+    const int lv = level[l];
     float x, y, z;
-    leaf_centre(key[l], level[l], g, &x, &y, &z);
+    leaf_centre(kl, lv, g, &x, &y, &z);
     int cnt = 0;
     for (int i = lane; i < F; i += 32) {
       float t;
-      cnt += eq1_sample(sc[i], depth + size_t(i) * H * W, H, W, x, y, z, g.delta, g.eta, &t);
+      cnt += tr.key ? tree_sample(tr, i, kl, lv, g.D, &t)
+                    : eq1_sample(sc[i], depth + size_t(i) * H * W, H, W, x, y, z, g.delta, g.eta, &t);
     }
     cnt = warp_sum_i(cnt);
     if (lane == 0) count[l] = uint32_t(cnt);
@@ -430,8 +445,9 @@ __global__ void __launch_bounds__(256) k_leaf_fill(
     const uint64_t* __restrict__ key, const uint8_t* __restrict__ level,
     const uint32_t* __restrict__ list, const unsigned long long* __restrict__ nlist, int64_t n,
     const float* __restrict__ depth,
-    const Cam* __restrict__ cams, int F, int H, int W, Geo g, const uint32_t* __restrict__ soff,
-    T* __restrict__ samp, float* __restrict__ u, float* __restrict__ ubar) {
+    const Cam* __restrict__ cams, int F, int H, int W, Geo g, FrameTrees tr,
+    const uint32_t* __restrict__ soff, T* __restrict__ samp, float* __restrict__ u,
+    float* __restrict__ ubar) {
   extern __shared__ float4 smem_dyn[];
   Cam* sc = reinterpret_cast<Cam*>(smem_dyn);
   float* bufs = reinterpret_cast<float*>(sc + F);
@@ -442,10 +458,18 @@ __global__ void __launch_bounds__(256) k_leaf_fill(
   for (int64_t j = int64_t(blockIdx.x) * kWarpsPerBlock + warp; j < n;
        j += int64_t(gridDim.x) * kWarpsPerBlock) {
     const int64_t l = list ? int64_t(list[j]) : j;
+    const uint64_t kl = key[l];
+    const int lv = level[l];
     float x, y, z;
-    leaf_centre(key[l], level[l], g, &x, &y, &z);
+    leaf_centre(kl, lv, g, &x, &y, &z);
     float mn, mx;
-    const int cnt = warp_samples<P>(sc, depth, F, H, W, x, y, z, g.delta, g.eta, a, &mn, &mx);
+    const int cnt = warp_samples_of<P>(
+        [&](int i, float* t) {
+          return tr.key ? tree_sample(tr, i, kl, lv, g.D, t)
+                        : eq1_sample(sc[i], depth + size_t(i) * H * W, H, W, x, y, z, g.delta,
+                                     g.eta, t);
+        },
+        F, a, &mn, &mx);
     __syncwarp();
     // equal observed samples (e.g. all saturated) need no sort; the others are
     // sorted with the unobserved (+inf) entries last
@@ -1459,13 +1483,13 @@ cudaError_t launch_emit_constructed(const uint32_t* flags, const uint32_t* pos, 
 
 cudaError_t launch_leaf_count(const uint64_t* key, const uint8_t* level, const uint32_t* list,
                               const unsigned long long* nlist, int64_t n, const float* depth,
-                              const Cam* cams, int F, int H, int W, Geo g, uint32_t* count,
-                              cudaStream_t s) {
+                              const Cam* cams, int F, int H, int W, Geo g, FrameTrees tr,
+                              uint32_t* count, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const size_t sm = size_t(F) * sizeof(Cam);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_leaf_count, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
   k_leaf_count<<<warp_grid(n), 32 * kWarpsPerBlock, sm, s>>>(key, level, list, nlist, n, depth,
-                                                              cams, F, H, W, g, count);
+                                                              cams, F, H, W, g, tr, count);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1473,12 +1497,13 @@ cudaError_t launch_leaf_count(const uint64_t* key, const uint8_t* level, const u
 template <int P, typename T>
 static cudaError_t leaf_fill_p(const uint64_t* key, const uint8_t* level, const uint32_t* list,
                                const unsigned long long* nlist, int64_t n, const float* depth,
-                               const Cam* cams, int F, int H, int W, Geo g, const uint32_t* soff,
-                               void* samp, float* u, float* ubar, cudaStream_t s) {
+                               const Cam* cams, int F, int H, int W, Geo g, FrameTrees tr,
+                               const uint32_t* soff, void* samp, float* u, float* ubar,
+                               cudaStream_t s) {
   const size_t sm = size_t(F) * sizeof(Cam) + size_t(kWarpsPerBlock) * P * sizeof(float);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_leaf_fill<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
   k_leaf_fill<P, T><<<warp_grid(n), 32 * kWarpsPerBlock, sm, s>>>(
-      key, level, list, nlist, n, depth, cams, F, H, W, g, soff, reinterpret_cast<T*>(samp), u, ubar);
+      key, level, list, nlist, n, depth, cams, F, H, W, g, tr, soff, reinterpret_cast<T*>(samp), u, ubar);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1486,25 +1511,27 @@ static cudaError_t leaf_fill_p(const uint64_t* key, const uint8_t* level, const 
 template <typename T>
 static cudaError_t leaf_fill_t(const uint64_t* key, const uint8_t* level, const uint32_t* list,
                                const unsigned long long* nlist, int64_t n, const float* depth,
-                               const Cam* cams, int F, int H, int W, Geo g, const uint32_t* soff,
-                               void* samp, float* u, float* ubar, cudaStream_t s) {
+                               const Cam* cams, int F, int H, int W, Geo g, FrameTrees tr,
+                               const uint32_t* soff, void* samp, float* u, float* ubar,
+                               cudaStream_t s) {
   switch (pad_frames(F)) {
-    case 32: return leaf_fill_p<32, T>(key, level, list, nlist, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
-    case 64: return leaf_fill_p<64, T>(key, level, list, nlist, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
-    case 128: return leaf_fill_p<128, T>(key, level, list, nlist, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
-    case 256: return leaf_fill_p<256, T>(key, level, list, nlist, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
-    case 512: return leaf_fill_p<512, T>(key, level, list, nlist, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
+    case 32: return leaf_fill_p<32, T>(key, level, list, nlist, n, depth, cams, F, H, W, g, tr, soff, samp, u, ubar, s);
+    case 64: return leaf_fill_p<64, T>(key, level, list, nlist, n, depth, cams, F, H, W, g, tr, soff, samp, u, ubar, s);
+    case 128: return leaf_fill_p<128, T>(key, level, list, nlist, n, depth, cams, F, H, W, g, tr, soff, samp, u, ubar, s);
+    case 256: return leaf_fill_p<256, T>(key, level, list, nlist, n, depth, cams, F, H, W, g, tr, soff, samp, u, ubar, s);
+    case 512: return leaf_fill_p<512, T>(key, level, list, nlist, n, depth, cams, F, H, W, g, tr, soff, samp, u, ubar, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_leaf_fill(const uint64_t* key, const uint8_t* level, const uint32_t* list,
                              const unsigned long long* nlist, int64_t n, const float* depth,
-                             const Cam* cams, int F, int H, int W, Geo g, const uint32_t* soff,
-                             void* samp, bool fp16, float* u, float* ubar, cudaStream_t s) {
+                             const Cam* cams, int F, int H, int W, Geo g, FrameTrees tr,
+                             const uint32_t* soff, void* samp, bool fp16, float* u, float* ubar,
+                             cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  return fp16 ? leaf_fill_t<__half>(key, level, list, nlist, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s)
-              : leaf_fill_t<float>(key, level, list, nlist, n, depth, cams, F, H, W, g, soff, samp, u, ubar, s);
+  return fp16 ? leaf_fill_t<__half>(key, level, list, nlist, n, depth, cams, F, H, W, g, tr, soff, samp, u, ubar, s)
+              : leaf_fill_t<float>(key, level, list, nlist, n, depth, cams, F, H, W, g, tr, soff, samp, u, ubar, s);
 }
 
 cudaError_t launch_nbr_count(View v, Carry cy, int32_t* nbr, uint32_t* ovf_count, uint32_t* longq,

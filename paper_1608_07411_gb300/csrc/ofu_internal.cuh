@@ -128,6 +128,55 @@ __device__ __forceinline__ bool eq1_sample(const Cam& k, const float* __restrict
   return true;
 }
 
+// Per-frame TSDF octrees (Fig. 4 data term; built by frames.cu): the tree
+// leaves of every frame sorted by key, frame i at [start[i], start[i + 1]),
+// with observed counts and float64 sums of f, and exclusive prefix sums of
+// both over the concatenation.  key == nullptr: Eq. 1 at leaf centres.
+struct FrameTrees {
+  const int64_t* start = nullptr;   // [F + 1]
+  const uint64_t* key = nullptr;
+  const uint8_t* level = nullptr;
+  const uint64_t* cnt = nullptr;
+  const double* tot = nullptr;
+  const uint64_t* pcnt = nullptr;   // [total + 1]
+  const double* ptot = nullptr;     // [total + 1]
+};
+
+// f_i* for the iterate leaf (key k, level L) by the Fig. 4 rule: the deepest
+// node of frame i's tree on the path to the leaf at a level <= L, its mean
+// when any voxel below it is observed.  Returns false when it is not
+// observed (w = 0).
+__device__ __forceinline__ bool tree_sample(const FrameTrees& t, int i, uint64_t k, int L, int D,
+                                            float* f) {
+  int64_t lo = t.start[i], hi = t.start[i + 1];
+  const int64_t end0 = hi;
+  while (lo < hi) {   // first tree leaf with key > k
+    const int64_t mid = (lo + hi) >> 1;
+    if (t.key[mid] <= k) lo = mid + 1; else hi = mid;
+  }
+  const int64_t j = lo - 1;   // the tree leaf holding voxel k (the first leaf has key 0)
+  uint64_t c;
+  double s;
+  if (t.level[j] <= L) {
+    c = t.cnt[j];
+    s = t.tot[j];
+  } else {
+    // the node at level L is an inner node: its leaves are the keys [k, k + 8^(D-L))
+    const uint64_t kend = k + (uint64_t(1) << (3 * (D - L)));
+    lo = j;
+    hi = end0;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (t.key[mid] < kend) lo = mid + 1; else hi = mid;
+    }
+    c = t.pcnt[lo] - t.pcnt[j];
+    s = t.ptot[lo] - t.ptot[j];
+  }
+  if (c == 0) return false;
+  *f = float(s / double(c));
+  return true;
+}
+
 // Leaf centre in float32: origin + (corner + h/2) * voxel.
 __device__ __forceinline__ float centre_coord(float org, uint32_t corner, uint32_t h, float vox) {
   const float mid = __fadd_rn(float(corner), __fmul_rn(0.5f, float(h)));
@@ -257,6 +306,17 @@ struct ofu_ctx {
   size_t scratch_bytes = 0;
   void* pinned = nullptr;  // small host staging for scalar results
 
+  // per-frame TSDF octrees (data_term = 1): see FrameTrees
+  int64_t* ft_start = nullptr;       // device [F + 1]
+  uint64_t* ft_key = nullptr;
+  uint8_t* ft_level = nullptr;
+  uint64_t* ft_cnt = nullptr;
+  double* ft_tot = nullptr;
+  uint64_t* ft_pcnt = nullptr;       // [cap + 1]
+  double* ft_ptot = nullptr;         // [cap + 1]
+  int64_t ft_cap = 0;
+  std::vector<int64_t> ft_host_start;  // host copy of ft_start
+
   // per-launch timing of the iteration kernels (ofu_profile)
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev;   // pool, 3 per iteration
@@ -303,12 +363,13 @@ cudaError_t launch_emit_constructed(const uint32_t* flags, const uint32_t* pos,
 // also writes u = ubar = median when u is given.
 cudaError_t launch_leaf_count(const uint64_t* key, const uint8_t* level, const uint32_t* list,
                               const unsigned long long* nlist, int64_t n, const float* depth,
-                              const Cam* cams, int F, int H, int W, Geo g, uint32_t* count,
-                              cudaStream_t s);
+                              const Cam* cams, int F, int H, int W, Geo g, FrameTrees tr,
+                              uint32_t* count, cudaStream_t s);
 cudaError_t launch_leaf_fill(const uint64_t* key, const uint8_t* level, const uint32_t* list,
                              const unsigned long long* nlist, int64_t n, const float* depth,
-                             const Cam* cams, int F, int H, int W, Geo g, const uint32_t* soff,
-                             void* samp, bool fp16, float* u, float* ubar, cudaStream_t s);
+                             const Cam* cams, int F, int H, int W, Geo g, FrameTrees tr,
+                             const uint32_t* soff, void* samp, bool fp16, float* u, float* ubar,
+                             cudaStream_t s);
 
 // Leaf classes of the iteration kernels, read from the unscanned
 // neighbour-list counts and listed in leaf order: heavy (dual: a +face list

@@ -509,18 +509,31 @@ __device__ __forceinline__ void leaf_terms(const uint32_t* __restrict__ soff,
   const uint32_t o = soff[l];
   const int W = int(soff[l + 1] - o);
   const double rc = 1.0 / (double(W) + gamma);
-  double data = 0.0;
-  for (int k = 0; k < W; ++k) data += fabs(ul - double(load_sample(samp, o + k)));
-  *sp += vol * (rc * data + lambda * sqrt(g2));
-  // dual term: first k with slope c (2k - W) - dv >= 0, i.e. k >= (W + dv / c) / 2
-  double xs;
+  // dual term: first k with slope c (2k - W) - dv >= 0, i.e. k >= (W + dv / c) / 2;
+  // the minimiser is -1 before the first sample, +1 after the last, else f_(k-1)
   const double kk = ceil((double(W) + dv * (double(W) + gamma)) * 0.5);
-  if (kk <= 0.0) xs = -1.0;
-  else if (kk > double(W)) xs = 1.0;
-  else xs = double(load_sample(samp, o + int(kk) - 1));
-  xs = fmin(1.0, fmax(-1.0, xs));
-  double dd = 0.0;
-  for (int k = 0; k < W; ++k) dd += fabs(xs - double(load_sample(samp, o + k)));
+  const int mx = kk <= 0.0 ? 0 : (kk > double(W) ? W : int(kk) - 1);
+  const double xs = kk <= 0.0 ? -1.0 : (kk > double(W) ? 1.0 : double(load_sample(samp, o + mx)));
+  // With the samples sorted, sum_k |x - f_k| = x (2 m - W) + sum_k f_k - 2 sum_{k<m} f_k for
+  // any m splitting them into f_k <= x (k < m) and f_k >= x (k >= m).  One pass gives
+  // the total and the two prefix sums (m = #{f_k < u} for the primal term, m = mx for the
+  // dual term), so each sample costs one float64 addition.
+  double tot = 0.0, su = 0.0, sx = 0.0;
+  int mu = W;
+  for (int k = 0; k < W; ++k) {
+    const double f = double(load_sample(samp, o + k));
+    if (mu == W && !(f < ul)) {
+      mu = k;
+      su = tot;
+    }
+    if (k == mx) sx = tot;
+    tot += f;
+  }
+  if (mu == W) su = tot;
+  if (mx == W) sx = tot;
+  const double data = ul * double(2 * mu - W) + tot - 2.0 * su;
+  const double dd = xs * double(2 * mx - W) + tot - 2.0 * sx;
+  *sp += vol * (rc * data + lambda * sqrt(g2));
   *sd += vol * (rc * dd - xs * dv);
 }
 

@@ -35,6 +35,8 @@ class Params(ctypes.Structure):
         ("tau_join", ctypes.c_double),
         ("spread_tau", ctypes.c_double),
         ("max_leaves", ctypes.c_int64),
+        ("data_term", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -68,6 +70,9 @@ _SIGS = {
     "ofu_iterate": (_i32, [_vp, _i32]),
     "ofu_descend": (_i32, [_vp, _i32, _i32, _d, _d, _i32]),
     "ofu_quantisation_error": (_i32, [_vp, _vp, _i64, _PD]),
+    "ofu_extract_mesh": (_i32, [_vp, _vp, _i64, _vp, _i64, _P64, _P64]),
+    "ofu_export_frame_tree": (_i32, [_vp, _i32, _vp, _vp, _i64, _P64]),
+    "ofu_data_term_memory": (_i32, [_vp, _vp, _P64, _P64, _P64]),
     "ofu_restructure": (_i32, [_vp, _P64, _P64, _P64]),
     "ofu_energy": (_i32, [_vp, _PD, _PD, _PD]),
     "ofu_num_leaves": (_i32, [_vp, _P64]),
@@ -204,6 +209,26 @@ def ofu_quantisation_error(ctx, fine, n_fine: int) -> float:
     return err.value
 
 
+def ofu_extract_mesh(ctx, verts=None, vcap=0, tris=None, tcap=0):
+    nv, nt = ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, load().ofu_extract_mesh(ctx, _ptr(verts), vcap, _ptr(tris), tcap, ctypes.byref(nv),
+                                        ctypes.byref(nt)))
+    return nv.value, nt.value
+
+
+def ofu_export_frame_tree(ctx, frame, keys=None, levels=None, cap=0) -> int:
+    n = ctypes.c_int64()
+    _check(ctx, load().ofu_export_frame_tree(ctx, frame, _ptr(keys), _ptr(levels), cap, ctypes.byref(n)))
+    return n.value
+
+
+def ofu_data_term_memory(ctx, nodes=None):
+    d, o, v = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, load().ofu_data_term_memory(ctx, _ptr(nodes), ctypes.byref(d), ctypes.byref(o),
+                                            ctypes.byref(v)))
+    return d.value, o.value, v.value
+
+
 def ofu_restructure(ctx):
     a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     _check(ctx, load().ofu_restructure(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
@@ -337,8 +362,9 @@ def ofu_kernel_launches() -> int:
     return int(load().ofu_kernel_launches())
 
 
-def ofu_profile(ctx, enable: bool) -> None:
-    _check(ctx, load().ofu_profile(ctx, int(bool(enable))))
+def ofu_profile(ctx, enable) -> None:
+    """enable: False/0 stops; True/1, or an iteration count that sizes the event pool, starts."""
+    _check(ctx, load().ofu_profile(ctx, int(enable)))
 
 
 def ofu_profile_read(ctx):
@@ -353,8 +379,8 @@ def ofu_profile_read(ctx):
 # ---- convenience wrapper (host NumPy in / out) -------------------------------
 
 
-def params_for(scene, sample_fp16: bool = False, max_leaves: int = 0) -> Params:
-    """Params of a :class:`scenes.Scene`."""
+def params_for(scene, sample_fp16: bool = False, max_leaves: int = 0, frame_trees: bool = False) -> Params:
+    """Params of a :class:`scenes.Scene` (frame_trees: data_term = 1)."""
     p = Params()
     for k in range(3):
         p.origin[k] = float(scene.origin[k])
@@ -369,6 +395,7 @@ def params_for(scene, sample_fp16: bool = False, max_leaves: int = 0) -> Params:
     p.tau_join = float(scene.tau_join)
     p.spread_tau = float(scene.spread_tau)
     p.max_leaves = int(max_leaves)
+    p.data_term = int(bool(frame_trees))
     return p
 
 
@@ -412,6 +439,22 @@ class Octree:
 
     def restructure(self):
         return ofu_restructure(self.ctx)
+
+    def frame_tree(self, frame):
+        """(keys uint64, levels uint8) of one frame's TSDF octree (data_term = 1)."""
+        n = ofu_export_frame_tree(self.ctx, frame)
+        k = np.empty(max(n, 1), np.uint64)
+        lv = np.empty(max(n, 1), np.uint8)
+        ofu_export_frame_tree(self.ctx, frame, k, lv, n)
+        return k[:n], lv[:n]
+
+    def mesh(self):
+        """(vertices float32 [V, 3], triangles int32 [T, 3]) of the zero level set."""
+        nv, nt = ofu_extract_mesh(self.ctx)
+        v = np.empty((max(nv, 1), 3), np.float32)
+        t = np.empty((max(nt, 1), 3), np.int32)
+        ofu_extract_mesh(self.ctx, v, nv, t, nt)
+        return v[:nv], t[:nt]
 
     def energy(self):
         return ofu_energy(self.ctx)

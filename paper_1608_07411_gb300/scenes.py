@@ -23,7 +23,10 @@ available, so these scenes stand in for them):
                   1.2 (fx=fy=600), N(0, 2 mm) noise plus 1 % outlier pixels
                   uniform in [0.5, 2.0] m, D_max=8.
   * "at_scale"    5 seeded spheres/tori/boxes in [-1,1]^3, 100 views 640x480
-                  at distance 3.0, noise N(0, (0.0015 z^2) m), D_max=9.
+                  at distance 3.0, noise N(0, (0.0015 z^2) m), D_max=9; solved
+                  to a relative primal-dual gap below 1e-5: split/join every
+                  10 iterations during the first 500, then on that structure
+                  with the gap checked every 50 iterations (cap 20000).
 Every scene takes keyword overrides (frames, width, height, max_depth, ...)
 so tests can build the same kind of scene at a size a CPU finishes quickly.
 """
@@ -57,6 +60,8 @@ class Scene:
     iters: int                 # iteration count of the workload
     restructure_every: int
     gap_tol: float             # relative primal-dual gap stop (0 = fixed count)
+    refine_iters: int = 0      # with gap_tol: split/join only during these first iterations
+    gap_check_every: int = 0   # with gap_tol: iterations between gap checks once refined
 
     @property
     def frames(self) -> int:
@@ -226,13 +231,16 @@ def make_scene(name: str, seed: int = 0, **over) -> Scene:
     """Render the named workload with a seed; keyword overrides shrink it."""
     if name == "sphere":
         cfg = dict(frames=8, width=160, height=120, focal=140.0, dist=1.5,
-                   max_depth=6, extent=1.0, iters=200, gap_tol=0.0)
+                   max_depth=6, extent=1.0, iters=200, gap_tol=0.0, refine_iters=0,
+                   gap_check_every=0)
     elif name == "torus_box":
         cfg = dict(frames=32, width=640, height=480, focal=600.0, dist=1.2,
-                   max_depth=8, extent=1.0, iters=500, gap_tol=0.0)
+                   max_depth=8, extent=1.0, iters=500, gap_tol=0.0, refine_iters=0,
+                   gap_check_every=0)
     elif name == "at_scale":
         cfg = dict(frames=100, width=640, height=480, focal=600.0, dist=3.0,
-                   max_depth=9, extent=2.0, iters=2000, gap_tol=1e-5)
+                   max_depth=9, extent=2.0, iters=20000, gap_tol=1e-5, refine_iters=500,
+                   gap_check_every=50)
     else:
         raise ValueError(f"unknown workload {name!r}; choose from {WORKLOADS}")
     cfg.update(lam=0.5, gamma=1e-3, tau_split=0.95, tau_join=0.99, spread_tau=0.1,
@@ -297,4 +305,5 @@ def make_scene(name: str, seed: int = 0, **over) -> Scene:
                  gamma=float(cfg["gamma"]), tau_split=float(cfg["tau_split"]),
                  tau_join=float(cfg["tau_join"]), spread_tau=float(cfg["spread_tau"]),
                  iters=int(cfg["iters"]), restructure_every=int(cfg["restructure_every"]),
-                 gap_tol=float(cfg["gap_tol"]))
+                 gap_tol=float(cfg["gap_tol"]), refine_iters=int(cfg["refine_iters"]),
+                 gap_check_every=int(cfg["gap_check_every"]))

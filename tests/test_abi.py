@@ -50,14 +50,15 @@ def test_params_layout_matches_header(lib):
     assert p.max_depth == 6 and p.extent == 1.0 and p.spread_tau == 0.1
     assert abs(p.delta - 4 / 64) < 1e-15 and abs(p.eta - 8 / 64) < 1e-15
     assert p.lambda_ == 0.5 and p.gamma == 1e-3 and p.tau_split == 0.95 and p.tau_join == 0.99
-    assert list(p.origin) == [-0.5, -0.5, -0.5] and p.max_leaves == 0
-    assert ctypes.sizeof(octfuse.Params) == 3 * 8 + 8 + 4 + 4 + 7 * 8 + 8
+    assert list(p.origin) == [-0.5, -0.5, -0.5] and p.max_leaves == 0 and p.data_term == 0
+    assert ctypes.sizeof(octfuse.Params) == 3 * 8 + 8 + 4 + 4 + 7 * 8 + 8 + 4 + 4
 
 
 @pytest.mark.parametrize("field,value,msg", [
     ("max_depth", 0, "max_depth"), ("max_depth", 16, "max_depth"), ("extent", -1.0, "extent"),
     ("delta", 0.0, "delta"), ("gamma", 0.0, "gamma"), ("lambda_", float("nan"), "lambda"),
     ("tau_join", 0.5, "tau_join"), ("sample_fp16", 2, "sample_fp16"), ("max_leaves", -5, "max_leaves"),
+    ("data_term", 2, "data_term"), ("reserved", 1, "reserved"),
 ])
 def test_invalid_params_rejected_on_host(lib, field, value, msg):
     p = octfuse.ofu_default_params()

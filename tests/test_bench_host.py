@@ -53,13 +53,15 @@ def test_clock_record_without_uuid_match_uses_every_row(monkeypatch):
 
 def test_traffic_is_scaled_and_dropped_when_the_kernel_changes(monkeypatch):
     t = json.load(open(bench.os.path.join(bench.ROOT, "profiles", "traffic.json")))
-    rec = t["k_primal"]
+    wl = next(k for k in t if not k.startswith("_"))
+    rec = t[wl]["k_primal"]
     monkeypatch.setattr(bench, "kernel_source_sha", lambda: rec["source_sha"])
-    got = bench.measured_traffic("k_primal", 2 * rec["alg_bytes_per_launch"])
+    got = bench.measured_traffic("k_primal", wl, 2 * rec["alg_bytes_per_launch"])
     assert got == pytest.approx(2 * rec["dram_bytes_per_launch"])
+    assert bench.measured_traffic("k_primal", "no_such_workload", 1.0) is None
     monkeypatch.setattr(bench, "kernel_source_sha", lambda: "0" * 16)
-    assert bench.measured_traffic("k_primal", rec["alg_bytes_per_launch"]) is None
-    assert bench.measured_traffic("no_such_kernel", 1.0) is None
+    assert bench.measured_traffic("k_primal", wl, rec["alg_bytes_per_launch"]) is None
+    assert bench.measured_traffic("no_such_kernel", wl, 1.0) is None
 
 
 def test_peak_from_measured_file_else_fallback(monkeypatch, tmp_path):
