@@ -69,6 +69,7 @@ def args_():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-tte", action="store_true", help="skip the time-to-energy measurement")
     ap.add_argument("--no-precision", action="store_true", help="skip the float16/float32 field errors")
+    ap.add_argument("--no-study", action="store_true", help="skip the Eq. 7 quantisation-error study")
     return ap.parse_args()
 
 
@@ -570,6 +571,75 @@ def precision(a, scene, of, torch, dev, iters=100):
     return out
 
 
+def quantisation_study(scene, of, torch, dev, checkpoints=(10, 20, 50, 100, 200, 500), sweep_iters=200):
+    """Eq. 7 and Sec. 4.2 (Fig. 10 / 11) on the GPU: the quantisation error
+    between the adaptive solve (split/join every R iterations) and a fully
+    refined run of the same scan (every leaf at D_max: construction threshold
+    below 0, no split or join), at the given iteration counts; then a sweep of
+    the split and join thresholds with the leaf count, primal energy and the
+    error against the fully refined run after `sweep_iters` iterations."""
+    g = Gpu(scene, of, torch, dev)
+    R = scene.restructure_every
+    D = scene.max_depth
+    nf = 8 ** D
+
+    def ctx(**kw):
+        p = of.params_for(scene)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        c = of.ofu_create_octree(p, g.stream.cuda_stream)
+        g.integrate(c)
+        return c
+
+    fine = torch.empty(nf, dtype=torch.float32, device=dev)
+    ev0 = g.event()
+    dense = ctx(spread_tau=-1.0, tau_split=2.0, tau_join=2.0)
+    nd = of.ofu_num_leaves(dense)
+    assert nd == nf
+    adap = ctx()
+    rows, done = [], 0
+    for t in checkpoints:
+        while done < t:
+            of.ofu_iterate(dense, R)
+            of.ofu_iterate(adap, R)
+            done += R
+            if done < t:
+                of.ofu_restructure(adap)
+        of.ofu_export_field(dense, of.FIELD_U, fine.data_ptr(), nf)
+        err = of.ofu_quantisation_error(adap, fine.data_ptr(), nf)
+        n = of.ofu_num_leaves(adap)
+        Pa, _, Ga = of.ofu_energy(adap)
+        Pd, _, Gd = of.ofu_energy(dense)
+        rows.append({"iteration": t, "leaves": n, "eq7_error": err, "eq7_error_per_leaf": err / n,
+                     "energy_adaptive": Pa, "energy_dense": Pd, "rel_gap_adaptive": Ga / max(abs(Pa), 1),
+                     "rel_gap_dense": Gd / max(abs(Pd), 1)})
+        if done < checkpoints[-1]:
+            of.ofu_restructure(adap)
+        if t == sweep_iters:
+            fine_sweep = fine.clone()
+            Pd_sweep = Pd
+    of.ofu_destroy(adap)
+    of.ofu_destroy(dense)
+    sweep = []
+    for ts in (0.5, 0.8, 0.9, 0.95):
+        for tj in (0.95, 0.99, 1.01):
+            if tj < ts:
+                continue
+            c = ctx(tau_split=ts, tau_join=tj)
+            of.ofu_solve(c, sweep_iters, R, 0, 0.0)
+            P, _, G = of.ofu_energy(c)
+            err = of.ofu_quantisation_error(c, fine_sweep.data_ptr(), nf)
+            n = of.ofu_num_leaves(c)
+            sweep.append({"tau_split": ts, "tau_join": tj, "joins": tj <= 1.0, "leaves": n,
+                          "energy": P, "energy_vs_dense": P / Pd_sweep - 1.0, "eq7_error": err,
+                          "eq7_error_per_leaf": err / n})
+            of.ofu_destroy(c)
+    ev1 = g.event()
+    ev1.synchronize()
+    return {"workload": scene.name, "dense_leaves": nd, "adaptive_vs_dense": rows,
+            "sweep_iterations": sweep_iters, "sweep": sweep, "ms": ev0.elapsed_time(ev1)}
+
+
 def aggregate(dist, total_ms, work, device):
     """Whole-job figures of a multi-rank run: the step time is the slowest
     rank's, the work (leaf-iterations) the sum over ranks.  Without a process
@@ -660,6 +730,12 @@ def main():
             make_scene("torus_box", a.seed)
         prec = precision(a, pscene, of, torch, dev)
 
+    study = None
+    if not a.no_study and rank == 0:
+        sscene = sec_scene if sec_scene is not None and sec_scene.name == "torus_box" else \
+            make_scene("torus_box", a.seed)
+        study = quantisation_study(sscene, of, torch, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         r = cpu_rate(scene, a.cpu_seconds)
@@ -687,6 +763,7 @@ def main():
             "roofline": roofline(res, scene.name), "clocks": clk, "cpu_baseline": cpu,
             "iterate_only": res["iterate_only"], "construction": res["construction"],
             "time_to_energy": tte, "precision": prec, "second_workload": second,
+            "quantisation_study": study,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -47,3 +47,44 @@ def test_at_scale_workload():
     k2, lv2, _ = o.leaves()
     assert octree.check_tiling(k2, lv2, D)
     o.close()
+
+
+def test_at_scale_one_iteration_after_restructure():
+    """After three windows and a split/join pass at D_max = 9 (heavy leaves
+    and long lists included): the GPU's structure tables equal the oracle's
+    built from the GPU's leaves, and one more GPU iteration equals the
+    oracle's iteration from the same float32 state on every leaf."""
+    from oracle import solver
+    scene = make_scene("at_scale", 1)
+    o = octfuse.Octree(octfuse.params_for(scene))
+    o.integrate_frames(scene.depth, scene.intr, scene.pose)
+    o.solve(30, scene.restructure_every, 0, 0.0)
+    o.restructure()
+    o.iterate(2)
+    k, lv, _ = o.leaves()
+    off = o.field(octfuse.FIELD_SAMPLE_OFF).astype(np.int64)
+    s = o.field(octfuse.FIELD_SAMPLES)
+    W = np.diff(off)
+    fs = np.full((len(k), int(W.max())), np.nan)
+    rows = np.repeat(np.arange(len(k)), W)
+    fs[rows, np.arange(len(s)) - np.repeat(off[:-1], W)] = s
+    st = solver.State(dmax=scene.max_depth, keys=k, levels=lv, fs=fs, W=W.astype(np.int64),
+                      u=None, ubar=None, p=None, lam=scene.lam, gamma=scene.gamma)
+    st.rebuild_operators()
+    gn = o.neighbours()
+    for f in range(6):
+        np.testing.assert_array_equal(gn[f][0], st.nbrs[f][0])
+        np.testing.assert_array_equal(gn[f][1], st.nbrs[f][1])
+    np.testing.assert_allclose(o.field(octfuse.FIELD_TAU), st.tau, rtol=2e-5)
+    np.testing.assert_allclose(o.field(octfuse.FIELD_SIGMA), st.sigma, rtol=2e-5)
+    st.u = o.field(octfuse.FIELD_U).astype(np.float64)
+    st.ubar = o.field(octfuse.FIELD_UBAR).astype(np.float64)
+    st.p = o.field(octfuse.FIELD_P).astype(np.float64)
+    P, D, G = o.energy()
+    Po, Do, _ = solver.energies(st)
+    assert abs(P - Po) <= 1e-9 * abs(Po) and abs(D - Do) <= 1e-9 * abs(Po)
+    o.iterate(1)
+    solver.step(st, 1)
+    np.testing.assert_allclose(o.field(octfuse.FIELD_U), st.u, atol=2e-6, rtol=0)
+    np.testing.assert_allclose(o.field(octfuse.FIELD_P), st.p, atol=2e-6, rtol=0)
+    o.close()

@@ -44,3 +44,45 @@ def test_quantisation_error_matches_oracle():
         assert e.value.status == octfuse.OFU_EINVAL
     finally:
         o.close()
+
+
+def _ctx(scene, **kw):
+    p = octfuse.params_for(scene)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    o = octfuse.Octree(p)
+    o.integrate_frames(scene.depth, scene.intr, scene.pose)
+    return o
+
+
+@pytest.mark.parametrize("name,kw", [("sphere", dict(frames=6, width=96, height=72, max_depth=5)),
+                                     ("torus_box", dict(frames=10, width=128, height=96, max_depth=6))])
+def test_adaptive_against_fully_refined_run(name, kw):
+    """The Sec. 4.2 study on the GPU: Eq. 7 between the adaptive solve and a
+    fully refined run of the same scan, along the iterations, equals the
+    oracle's Eq. 7 of the same exported fields; a run with splitting forced
+    to the finest level and joins disabled is the fully refined run itself
+    (error exactly 0)."""
+    scene = make_scene(name, 7, **kw)
+    D = scene.max_depth
+    dense = _ctx(scene, spread_tau=-1.0, tau_split=2.0, tau_join=2.0)
+    same = _ctx(scene, spread_tau=-1.0, tau_split=2.0, tau_join=2.0)
+    adap = _ctx(scene)
+    kd, lvd, _ = dense.leaves()
+    assert len(kd) == 8 ** D and np.array_equal(kd, np.arange(8 ** D)) and np.all(lvd == D)
+    errs = []
+    for window in range(1, 11):
+        for o in (dense, same, adap):
+            o.iterate(scene.restructure_every)
+        fine = dense.field(octfuse.FIELD_U)
+        k, lv, u = adap.leaves()
+        err = adap.quantisation_error(fine)
+        ref = quantisation.error(k, lv, D, u, fine.astype(np.float64))
+        assert abs(err - ref) <= 1e-9 * max(ref, 1.0), (window, err, ref)
+        assert same.quantisation_error(fine) == 0.0
+        errs.append(err)
+        adap.restructure()
+        same.restructure()
+    assert errs[-1] > 0
+    for o in (dense, same, adap):
+        o.close()
