@@ -70,6 +70,7 @@ def args_():
     ap.add_argument("--no-tte", action="store_true", help="skip the time-to-energy measurement")
     ap.add_argument("--no-precision", action="store_true", help="skip the float16/float32 field errors")
     ap.add_argument("--no-study", action="store_true", help="skip the Eq. 7 quantisation-error study")
+    ap.add_argument("--no-descent", action="store_true", help="skip the eps-L1 descent line")
     return ap.parse_args()
 
 
@@ -571,6 +572,32 @@ def precision(a, scene, of, torch, dev, iters=100):
     return out
 
 
+def descent_line(a, scene, of, torch, dev, flush, iters=100):
+    """The paper's own solver (Eq. 4-6, Sec. 4: eps-L1 gradient descent, step
+    0.1 halved every 20, 100 iterations) on the same scan: device time of the
+    iterations alone after construction, steps as the main measurement."""
+    g = Gpu(scene, of, torch, dev)
+    c = g.ctx(a.fp16)
+    times, li = [], 0
+    for k in range(max(a.warmup, 0) + a.steps):
+        g.integrate(c)
+        n = of.ofu_num_leaves(c)
+        flush.zero_()
+        e0 = g.event()
+        of.ofu_descend(c, iters, 0, 1e-3, 0.1, 20)
+        e1 = g.event()
+        e1.synchronize()
+        if k >= a.warmup:
+            times.append(e0.elapsed_time(e1))
+            li += n * iters
+    P, _, _ = of.ofu_energy(c)
+    of.ofu_destroy(c)
+    return {"workload": scene.name, "value": li / (sum(times) * 1e-3), "unit": METRIC,
+            "iterations": iters, "ms": statistics.median(times), "leaves": n,
+            "us_per_iteration": 1e3 * statistics.median(times) / iters,
+            "energy_after": P, "schedule": "eps 1e-3, xi 0.1 halved every 20 (no split/join)"}
+
+
 def quantisation_study(scene, of, torch, dev, checkpoints=(10, 20, 50, 100, 200, 500), sweep_iters=200):
     """Eq. 7 and Sec. 4.2 (Fig. 10 / 11) on the GPU: the quantisation error
     between the adaptive solve (split/join every R iterations) and a fully
@@ -724,6 +751,8 @@ def main():
                   "roofline": roofline(r2, sec_scene.name), "construction": r2["construction"]}
 
     tte = None if a.no_tte or rank != 0 else time_to_energy(a, scene, of, torch, dev)
+    desc = [descent_line(a, sc, of, torch, dev, flush) for sc in (scene, sec_scene) if sc is not None] \
+        if rank == 0 and not a.no_descent else None
     prec = None
     if not a.no_precision and rank == 0:
         pscene = sec_scene if sec_scene is not None and sec_scene.name == "torus_box" else \
@@ -763,7 +792,7 @@ def main():
             "roofline": roofline(res, scene.name), "clocks": clk, "cpu_baseline": cpu,
             "iterate_only": res["iterate_only"], "construction": res["construction"],
             "time_to_energy": tte, "precision": prec, "second_workload": second,
-            "quantisation_study": study,
+            "quantisation_study": study, "descent": desc,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -773,7 +773,7 @@ ofu_status ofu_descend(ofu_ctx* ctx, int32_t n, int32_t t0, double eps, double x
     const double xi = xi0 * std::ldexp(1.0, -int(std::min<int64_t>(t / halve_every, 2000)));
     CU(launch_descent_step(v, L.u, L.ubar, q, L.soff, ctx->samp[ctx->cur], ctx->prm.sample_fp16 != 0,
                            float(eps), float(xi), float(ctx->prm.lambda), float(ctx->prm.gamma),
-                           ctx->stream));
+                           dual_sets(ctx), primal_sets(ctx), ctx->stream));
   }
   return OFU_OK;
 }

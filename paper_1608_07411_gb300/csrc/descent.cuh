@@ -11,6 +11,7 @@ namespace ofu {
 // ubar <- u.  Two launches on `s`.
 cudaError_t launch_descent_step(View v, float* u, float* ubar, float* q, const uint32_t* soff,
                                 const void* samp, bool fp16, float eps, float xi, float lambda,
-                                float gamma, cudaStream_t s);
+                                float gamma, LeafSets dual_sets, LeafSets primal_sets,
+                                cudaStream_t s);
 
 }  // namespace ofu

@@ -10,68 +10,11 @@
 // divergence gathers from the -face lists and nothing is scattered.
 #include <math_constants.h>
 
-#include "ofu_internal.cuh"
+#include "stencil.cuh"
 
 namespace ofu {
 
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-constexpr int kThreads = 256;
-// Resident blocks per SM the iteration kernels are compiled for.  Without a
-// stated minimum the compiler caps them at 32 registers and spills (the heavy
-// path's block reductions share the register budget); 6 blocks (<= 42
-// registers) measured fastest over 4..8 on both the 256^3 and 512^3 workloads.
-constexpr int kIterMinBlocks = 6;
-
-__device__ __forceinline__ float edge_f(int D, int level) { return float(1u << (D - level)); }
-
-// 1 / Delta for leaves of edges h and hm: 2 / (h + hm), exact sum of powers of two.
-__device__ __forceinline__ float inv_delta(float h, float hm) { return __fdividef(2.0f, h + hm); }
-
-template <typename T>
-__device__ __forceinline__ float load_sample(const T* s, uint32_t i) {
-  if constexpr (sizeof(T) == 2)
-    return __half2float(s[i]);
-  else
-    return s[i];
-}
-
-// Leaves with a face list longer than kHeavy are updated by one block each
-// (the octree is not 2:1 balanced: a coarse leaf can face hundreds of finest
-// leaves); the thread-per-leaf path leaves them alone.  A launch runs the
-// heavy blocks first, then the per-leaf blocks.
-constexpr int kHeavyThreads = kThreads;   // a heavy leaf's block is a full launch block
-
-// Fixed-order block sum of one float per thread (kHeavyThreads threads).
-__device__ __forceinline__ float block_sum(float x, float* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
-  __syncthreads();
-  float t = 0.0f;
-#pragma unroll
-  for (int w = 0; w < kHeavyThreads / 32; ++w) t += red[w];
-  return t;
-}
-
-__device__ __forceinline__ void dual_write(float* __restrict__ p, int64_t stride, int64_t l,
-                                           float s, const float g[3], float lambda) {
-  float q0 = p[l] + s * g[0];
-  float q1 = p[stride + l] + s * g[1];
-  float q2 = p[2 * stride + l] + s * g[2];
-  const float nrm = sqrtf(q0 * q0 + q1 * q1 + q2 * q2);
-  if (nrm > lambda) {
-    const float sc = lambda / nrm;
-    q0 *= sc;
-    q1 *= sc;
-    q2 *= sc;
-  }
-  p[l] = q0;
-  p[stride + l] = q1;
-  p[2 * stride + l] = q2;
-}
 
 // p of a piecewise-ramp field: lambda g / |g| where |g| >= g0, else 0 (the
 // optimal dual wherever the TV term is differentiable and the field has an
@@ -85,245 +28,129 @@ __device__ __forceinline__ void dual_init_write(float* __restrict__ p, int64_t s
   p[2 * stride + l] = sc * g[2];
 }
 
-// Sum over one face's finer-neighbour list of w(level) * val(index), in list
-// order.  The entries are loaded four at a time and their values gathered
-// four at a time, so a list of c entries costs about 2 ceil(c / 4) dependent
-// loads instead of 2 c.
-template <typename WFn, typename VFn>
-__device__ __forceinline__ float list_sum(const int32_t* __restrict__ lst, int cnt, WFn w, VFn val) {
-  float acc = 0.0f;
-  for (int k0 = 0; k0 < cnt; k0 += 4) {
-    int32_t f[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) f[j] = k0 + j < cnt ? lst[k0 + j] : 0;
-    float x[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) x[j] = k0 + j < cnt ? val(entry_idx(f[j])) : 0.0f;
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (k0 + j < cnt) acc += w(entry_level(f[j])) * x[j];
+// Dual-step value of leaf l from its gradient g: the ascent and projection,
+// or (INIT) the start lambda g / |g|.
+template <bool INIT>
+__device__ __forceinline__ void dual_finish(float* __restrict__ p, size_t st, int64_t l,
+                                            const float q[3], float sl, const float g[3],
+                                            float lambda, float g0) {
+  if (INIT) {
+    dual_init_write(p, int64_t(st), l, g, lambda, g0);
+    return;
   }
-  return acc;
+  float r0 = q[0] + sl * g[0], r1 = q[1] + sl * g[1], r2 = q[2] + sl * g[2];
+  const float nrm = sqrtf(r0 * r0 + r1 * r1 + r2 * r2);
+  if (nrm > lambda) {
+    const float sc = lambda / nrm;
+    r0 *= sc;
+    r1 *= sc;
+    r2 *= sc;
+  }
+  p[l] = r0;
+  p[st + l] = r1;
+  p[2 * st + l] = r2;
 }
 
-// Which leaf a thread of an iteration launch updates.  A launch is laid out as
-// [heavy blocks][list blocks][light blocks]: heavy leaves (a face list longer
-// than kHeavy) get a block each; "list" leaves (some face with finer
-// neighbours, none longer than kHeavy) a thread each over their compacted
-// index list, so their list walks do not hold up warps of plain leaves; every
-// other leaf a thread of the light blocks, which skip list leaves.  Returns
-// -1 for a thread with no leaf.
-struct Segments {
-  const uint32_t* heavy;
-  int n_heavy;
-  const uint32_t* list;
-  int n_list;
-};
+// Gradient of ubar at leaf l over its +face slots, this lane's share of a
+// group of G lanes (every neighbour term alpha (ubar_m - ubar_l) / Delta).
+__device__ __forceinline__ void grad_share(const View& v, const float* __restrict__ ubar, int64_t l,
+                                           const int32_t e[3], float h, float ul, int lane, int G,
+                                           float acc[3]) {
+  acc[0] = acc[1] = acc[2] = 0.0f;
+  for_each_slot<3>(v, e, lane, G, [&](int f, int32_t ent) {
+    const float t = plus_weight(h, edge_f(v.D, entry_level(ent))) * (ubar[entry_idx(ent)] - ul);
+    acc[0] += f == 0 ? t : 0.0f;
+    acc[1] += f == 1 ? t : 0.0f;
+    acc[2] += f == 2 ? t : 0.0f;
+  });
+}
 
-__device__ __forceinline__ int64_t segment_leaf(const Segments& sg, int64_t n, bool* is_list_leaf) {
-  const int lb = (sg.n_list + kThreads - 1) / kThreads;
-  const int b = int(blockIdx.x) - sg.n_heavy;
-  if (b < lb) {
-    const int j = b * kThreads + int(threadIdx.x);
-    *is_list_leaf = true;
-    return j < sg.n_list ? int64_t(sg.list[j]) : -1;
-  }
-  *is_list_leaf = false;
-  const int64_t l = int64_t(b - lb) * kThreads + threadIdx.x;
-  return l < n ? l : -1;
+// Lanes per list leaf of the dual and primal steps (measured over 1..16: 4
+// and 2 fastest on the 256^3 and 512^3 workloads; the primal step has about
+// twice as many list leaves, six faces and its prox).
+constexpr int kDualListLanes = 4;
+constexpr int kPrimalListLanes = 2;
+// Lanes per heavy leaf (a face list longer than kHeavy): one warp.
+constexpr int kHeavyLanes = 32;
+// Slots a lane of the primal step loads per round (registers allow 2 there).
+constexpr int kPrimalSlotBatch = 2;
+
+// Blocks of the heavy segment (kHeavyLanes lanes per heavy leaf).
+__device__ __host__ __forceinline__ int heavy_blocks(const Segments& sg) {
+  return (sg.n_heavy * kHeavyLanes + kThreads - 1) / kThreads;
+}
+
+// A dual step of the leaves of a compacted set (heavy or list leaves), G
+// lanes per leaf: the j-th leaf of `set` for threads j G .. j G + G - 1 of
+// the segment starting at block 0 + `b`.  Lanes past the end take the last
+// leaf and do not write (every lane of the warp joins the shuffles).
+template <bool INIT, int G>
+__device__ __forceinline__ void dual_group(const View& v, const float* __restrict__ ubar,
+                                           float* __restrict__ p, const float* __restrict__ sigma,
+                                           float lambda, float g0, const uint32_t* __restrict__ set,
+                                           int n_set, int b) {
+  const size_t st = size_t(v.stride);
+  const int t = b * kThreads + int(threadIdx.x);
+  const int j = t / G, lane = t % G;
+  const bool valid = j < n_set;
+  const int64_t l = set[valid ? j : n_set - 1];
+  const int32_t e[3] = {v.nbr[l], v.nbr[st + l], v.nbr[2 * st + l]};
+  const float h = edge_f(v.D, v.level[l]);
+  const float ul = ubar[l];
+  float acc[3];
+  grad_share(v, ubar, l, e, h, ul, lane, G, acc);
+  float g[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) g[d] = group_sum<G>(acc[d]);
+  if (lane != 0 || !valid) return;
+  const float q[3] = {p[l], p[st + l], p[2 * st + l]};
+  dual_finish<INIT>(p, st, l, q, INIT ? 0.0f : sigma[l], g, lambda, g0);
 }
 
 // INIT = false: the dual step p <- proj(p + sigma grad ubar).
 // INIT = true:  p <- dual_init_write(grad ubar) with threshold g0 (sigma unused).
+// Launch layout [heavy blocks][list blocks][light blocks]: a heavy leaf's
+// slots are spread over a warp, a list leaf's over kDualListLanes lanes, a
+// light leaf (single entries only) has a thread.
 template <bool INIT>
 __global__ void __launch_bounds__(kThreads, kIterMinBlocks) k_dual(View v, const float* __restrict__ ubar,
-                                                   float* __restrict__ p,
-                                                   const float* __restrict__ sigma, float lambda,
-                                                   Segments sg, float g0) {
-  if (int(blockIdx.x) < sg.n_heavy) {
-    // one heavy leaf per block; every thread takes part in the reductions
-    __shared__ float red[kHeavyThreads / 32];
-    const int64_t l = sg.heavy[blockIdx.x];
-    const float h = edge_f(v.D, v.level[l]);
-    const float ul = ubar[l];
-    float g[3];
-    for (int d = 0; d < 3; ++d) {
-      const int32_t e = v.nbr[int64_t(d) * v.stride + l];
-      float acc = 0.0f;
-      if (e >= 0) {
-        if (threadIdx.x == 0)
-          acc = (ubar[entry_idx(e)] - ul) * inv_delta(h, edge_f(v.D, entry_level(e)));
-      } else if (e != kEmpty) {
-        const uint32_t st = list_start(e);
-        const int cnt = v.ovf[st];
-        for (int k = threadIdx.x; k < cnt; k += kHeavyThreads) {
-          const int32_t f = v.ovf[st + 1 + k];
-          const float hm = edge_f(v.D, entry_level(f));
-          const float r = hm / h;
-          acc += r * r * (ubar[entry_idx(f)] - ul) * inv_delta(h, hm);
-        }
-      }
-      g[d] = block_sum(acc, red);
-    }
-    if (threadIdx.x == 0) {
-      if (INIT)
-        dual_init_write(p, v.stride, l, g, lambda, g0);
-      else
-        dual_write(p, v.stride, l, sigma[l], g, lambda);
-    }
+                                                                   float* __restrict__ p,
+                                                                   const float* __restrict__ sigma,
+                                                                   float lambda, Segments sg, float g0) {
+  const size_t st = size_t(v.stride);
+  const int hb = heavy_blocks(sg);
+  const int lb = (sg.n_list * kDualListLanes + kThreads - 1) / kThreads;
+  const int b = int(blockIdx.x);
+  if (b < hb + lb) {
+    if (b < hb)
+      dual_group<INIT, kHeavyLanes>(v, ubar, p, sigma, lambda, g0, sg.heavy, sg.n_heavy, b);
+    else
+      dual_group<INIT, kDualListLanes>(v, ubar, p, sigma, lambda, g0, sg.list, sg.n_list, b - hb);
     return;
   }
-  bool listed;
-  const int64_t l = segment_leaf(sg, v.n, &listed);
-  if (l < 0) return;
-  const size_t st = size_t(v.stride);
-  // every load that does not depend on another is issued before any branch
+  const int lbase = hb + lb;
+  // light path: one leaf per thread, single entries only; every load that does
+  // not depend on another is issued before any branch
+  const int64_t l = int64_t(b - lbase) * kThreads + threadIdx.x;
+  if (l >= v.n) return;
   const int32_t e[3] = {v.nbr[l], v.nbr[st + l], v.nbr[2 * st + l]};
   const int lev = v.level[l];
   const float h = edge_f(v.D, lev);
   const float ul = ubar[l];
   const float q[3] = {p[l], p[st + l], p[2 * st + l]};
   const float sl = INIT ? 0.0f : sigma[l];
+  // a list leaf's lane gathers its own value (harmless) and writes nothing
+  float x[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) x[d] = ubar[e[d] >= 0 ? entry_idx(e[d]) : uint32_t(l)];
   float g[3];
-  if (!listed) {
-    // light path: single entries only; a list leaf's lane gathers its own
-    // value (harmless) and writes nothing (its list thread does)
-    float x[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) x[d] = ubar[e[d] >= 0 ? entry_idx(e[d]) : uint32_t(l)];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const float hm = edge_f(v.D, e[d] >= 0 ? entry_level(e[d]) : lev);
-      g[d] = e[d] >= 0 ? (x[d] - ul) * inv_delta(h, hm) : 0.0f;
-    }
-    if (is_list(e[0]) || is_list(e[1]) || is_list(e[2])) return;
-  } else {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      float acc = 0.0f;
-      if (e[d] >= 0) {
-        // same or coarser neighbour: alpha = 1
-        acc = (ubar[entry_idx(e[d])] - ul) * inv_delta(h, edge_f(v.D, entry_level(e[d])));
-      } else if (e[d] != kEmpty) {
-        // finer neighbours: alpha = (h_m / h)^2
-        const uint32_t s0 = list_start(e[d]);
-        acc = list_sum(
-            v.ovf + s0 + 1, v.ovf[s0],
-            [&](int lev) {
-              const float hm = edge_f(v.D, lev);
-              const float r = hm / h;
-              return r * r * inv_delta(h, hm);
-            },
-            [&](uint32_t m) { return ubar[m] - ul; });
-      }
-      g[d] = acc;
-    }
-  }
-  if (INIT) {
-    dual_init_write(p, v.stride, l, g, lambda, g0);
-  } else {
-    float r0 = q[0] + sl * g[0], r1 = q[1] + sl * g[1], r2 = q[2] + sl * g[2];
-    const float nrm = sqrtf(r0 * r0 + r1 * r1 + r2 * r2);
-    if (nrm > lambda) {
-      const float sc = lambda / nrm;
-      r0 *= sc;
-      r1 *= sc;
-      r2 *= sc;
-    }
-    p[l] = r0;
-    p[st + l] = r1;
-    p[2 * st + l] = r2;
-  }
-}
-
-// Divergence of p at a list leaf l (gathers only; face lists of at most
-// kHeavy entries); q = p(l).
-__device__ __forceinline__ float divergence(const View& v, const float* __restrict__ p, int64_t l,
-                                            float h, const int32_t e[6], const float q[3]) {
-  float dv = 0.0f;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    float coef = 0.0f;
-    if (e[d] >= 0) {
-      coef = inv_delta(h, edge_f(v.D, entry_level(e[d])));
-    } else if (e[d] != kEmpty) {
-      const uint32_t st = list_start(e[d]);
-      const int32_t* lst = v.ovf + st + 1;
-      const int cnt = v.ovf[st];
-      for (int k = 0; k < cnt; ++k) {
-        const float hm = edge_f(v.D, entry_level(lst[k]));
-        const float r = hm / h;
-        coef += r * r * inv_delta(h, hm);
-      }
-    }
-    dv += coef * q[d];
+    const float hm = edge_f(v.D, e[d] >= 0 ? entry_level(e[d]) : lev);
+    g[d] = e[d] >= 0 ? (x[d] - ul) * inv_delta(h, hm) : 0.0f;
   }
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int32_t ed = e[3 + d];
-    const float* pd = p + int64_t(d) * v.stride;
-    if (ed >= 0) {
-      // same or coarser n: (h_n^3 / h^3) (h / h_n)^2 / Delta = (h_n / h) / Delta
-      const float hn = edge_f(v.D, entry_level(ed));
-      dv -= (hn / h) * inv_delta(h, hn) * pd[entry_idx(ed)];
-    } else if (ed != kEmpty) {
-      // finer n: alpha = 1, weight (h_n / h)^3 / Delta
-      const uint32_t st = list_start(ed);
-      dv -= list_sum(
-          v.ovf + st + 1, v.ovf[st],
-          [&](int lev) {
-            const float hn = edge_f(v.D, lev);
-            const float r = hn / h;
-            return r * r * r * inv_delta(h, hn);
-          },
-          [&](uint32_t m) { return pd[m]; });
-    }
-  }
-  return dv;
-}
-
-// The same divergence by one block (kHeavyThreads threads) of a heavy leaf;
-// the result is valid in every thread.
-__device__ float divergence_block(const View& v, const float* __restrict__ p, int64_t l, float h,
-                                  float* red) {
-  float dv = 0.0f;
-  for (int d = 0; d < 3; ++d) {
-    const int32_t e = v.nbr[int64_t(d) * v.stride + l];
-    float coef = 0.0f;
-    if (e >= 0) {
-      if (threadIdx.x == 0) coef = inv_delta(h, edge_f(v.D, entry_level(e)));
-    } else if (e != kEmpty) {
-      const uint32_t st = list_start(e);
-      const int cnt = v.ovf[st];
-      for (int k = threadIdx.x; k < cnt; k += kHeavyThreads) {
-        const float hm = edge_f(v.D, entry_level(v.ovf[st + 1 + k]));
-        const float r = hm / h;
-        coef += r * r * inv_delta(h, hm);
-      }
-    }
-    dv += block_sum(coef, red) * p[int64_t(d) * v.stride + l];
-  }
-  for (int d = 0; d < 3; ++d) {
-    const int32_t e = v.nbr[int64_t(3 + d) * v.stride + l];
-    float acc = 0.0f;
-    if (e >= 0) {
-      if (threadIdx.x == 0) {
-        const float hn = edge_f(v.D, entry_level(e));
-        acc = (hn / h) * inv_delta(h, hn) * p[int64_t(d) * v.stride + entry_idx(e)];
-      }
-    } else if (e != kEmpty) {
-      const uint32_t st = list_start(e);
-      const int cnt = v.ovf[st];
-      for (int k = threadIdx.x; k < cnt; k += kHeavyThreads) {
-        const int32_t f = v.ovf[st + 1 + k];
-        const float hn = edge_f(v.D, entry_level(f));
-        const float r = hn / h;
-        acc += r * r * r * inv_delta(h, hn) * p[int64_t(d) * v.stride + entry_idx(f)];
-      }
-    }
-    dv -= block_sum(acc, red);
-  }
-  return dv;
+  if (is_list(e[0]) || is_list(e[1]) || is_list(e[2])) return;
+  dual_finish<INIT>(p, st, l, q, sl, g, lambda, g0);
 }
 
 // Prox of the data term: argmin_x (x - v)^2 / (2 tau) + c sum_k |x - f_k| is
@@ -353,43 +180,127 @@ __device__ __forceinline__ float prox_l1(const T* __restrict__ f, int W, float v
   return fmaxf(flo, fminf(b, fhi));
 }
 
+// Divergence of p at leaf l over its six faces' slots, this lane's share of
+// a group of G lanes: +faces weigh p(l) by alpha / Delta per neighbour,
+// -faces subtract (h_n^3 / h^3) alpha_nl / Delta p(n).
+__device__ __forceinline__ float div_share(const View& v, const float* __restrict__ p, int64_t l,
+                                           const int32_t e[6], float h, const float q[3], int lane,
+                                           int G) {
+  float acc = 0.0f;
+  for_each_slot<6, kPrimalSlotBatch>(v, e, lane, G, [&](int f, int32_t ent) {
+    const float hm = edge_f(v.D, entry_level(ent));
+    if (f < 3) {
+      acc += plus_weight(h, hm) * (f == 0 ? q[0] : (f == 1 ? q[1] : q[2]));
+    } else {
+      acc -= minus_weight(h, hm) * p[int64_t(f - 3) * v.stride + entry_idx(ent)];
+    }
+  });
+  return acc;
+}
+
+// The prox of prox_l1 found by a group of G lanes: each round the lanes test
+// G evenly spaced ranks of [lo, hi) and the count of those that hold (a prefix,
+// the predicate being monotone) narrows the range, so a leaf of W samples
+// takes about log_G(W) rounds of independent loads.  k* is the same as the
+// bisection's, hence so is the result, in every lane.  The count is a warp
+// ballot (every lane of the warp takes part in every round).
+template <int G, typename T>
+__device__ __forceinline__ float prox_l1_group(const T* __restrict__ f, int W, float v, float t,
+                                               int lane) {
+  static_assert(G >= 1 && G <= 32 && (G & (G - 1)) == 0, "G lanes of one warp");
+  constexpr unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+  const unsigned gshift = (threadIdx.x & 31u) & ~unsigned(G - 1);
+  int lo = 0, hi = W;
+  for (;;) {
+    const bool active = lo < hi;
+    if (!__any_sync(kFull, active)) break;
+    const int step = active ? (hi - lo + G - 1) / G : 0;
+    const int q = lo + lane * step;
+    const bool ok = active && q < hi && load_sample(f, q) < __fmaf_rn(t, float(W - 2 * q), v);
+    const int c = __popc((__ballot_sync(kFull, ok) >> gshift) & gmask);
+    if (active) {
+      if (c == 0) {
+        hi = lo;
+      } else {
+        const int last = lo + (c - 1) * step;   // the last rank that holds
+        hi = min(hi, lo + c * step);             // the first that fails, if tested
+        lo = last + 1;
+      }
+    }
+  }
+  const float flo = lo > 0 ? load_sample(f, lo - 1) : -CUDART_INF_F;
+  const float fhi = lo < W ? load_sample(f, lo) : CUDART_INF_F;
+  const float b = __fmaf_rn(t, float(W - 2 * lo), v);
+  return fmaxf(flo, fminf(b, fhi));
+}
+
 template <typename T>
-__device__ __forceinline__ void primal_write(float* __restrict__ u, float* __restrict__ ubar,
-                                             int64_t l, float ul, float x, float tl,
-                                             const uint32_t* __restrict__ soff,
-                                             const T* __restrict__ samp, float gamma) {
-  const uint32_t o = soff[l];
-  const int W = int(soff[l + 1] - o);
+__device__ __forceinline__ void primal_finish(float* __restrict__ u, float* __restrict__ ubar,
+                                              int64_t l, float ul, float tl, float dv, uint32_t o,
+                                              int W, const T* __restrict__ samp, float gamma) {
+  const float x = ul + tl * dv;
   const float t = tl / (float(W) + gamma);
   const float un = fminf(fmaxf(prox_l1(samp + o, W, x, t), -1.0f), 1.0f);
   u[l] = un;
   ubar[l] = 2.0f * un - ul;
 }
 
+// A primal step of the leaves of a compacted set, G lanes per leaf (layout
+// as dual_group): the divergence over the slots and the prox by group search.
+template <int G, typename T>
+__device__ __forceinline__ void primal_group(const View& v, float* __restrict__ u,
+                                             float* __restrict__ ubar, const float* __restrict__ p,
+                                             const float* __restrict__ tau,
+                                             const uint32_t* __restrict__ soff,
+                                             const T* __restrict__ samp, float gamma,
+                                             const uint32_t* __restrict__ set, int n_set, int b) {
+  const int t = b * kThreads + int(threadIdx.x);
+  const int j = t / G, lane = t % G;
+  const bool valid = j < n_set;
+  const int64_t l = set[valid ? j : n_set - 1];
+  int32_t e[6];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) e[f] = v.nbr[int64_t(f) * v.stride + l];
+  const float h = edge_f(v.D, v.level[l]);
+  float q[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) q[d] = p[int64_t(d) * v.stride + l];
+  const uint32_t o = soff[l];
+  const int W = int(soff[l + 1] - o);
+  const float ul = u[l];
+  const float tl = tau[l];
+  const float dv = group_sum<G>(div_share(v, p, l, e, h, q, lane, G));
+  float un = prox_l1_group<G>(samp + o, W, ul + tl * dv, tl / (float(W) + gamma), lane);
+  if (lane != 0 || !valid) return;
+  un = fminf(fmaxf(un, -1.0f), 1.0f);
+  u[l] = un;
+  ubar[l] = 2.0f * un - ul;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads, kIterMinBlocks) k_primal(View v, float* __restrict__ u,
-                                                     float* __restrict__ ubar,
-                                                     const float* __restrict__ p,
-                                                     const float* __restrict__ tau,
-                                                     const uint32_t* __restrict__ soff,
-                                                     const T* __restrict__ samp, float gamma,
-                                                     Segments sg) {
-  if (int(blockIdx.x) < sg.n_heavy) {
-    __shared__ float red[kHeavyThreads / 32];
-    const int64_t l = sg.heavy[blockIdx.x];
-    const float h = edge_f(v.D, v.level[l]);
-    const float dv = divergence_block(v, p, l, h, red);
-    if (threadIdx.x == 0) {
-      const float tl = tau[l];
-      const float ul = u[l];
-      primal_write(u, ubar, l, ul, ul + tl * dv, tl, soff, samp, gamma);
-    }
+                                                                     float* __restrict__ ubar,
+                                                                     const float* __restrict__ p,
+                                                                     const float* __restrict__ tau,
+                                                                     const uint32_t* __restrict__ soff,
+                                                                     const T* __restrict__ samp,
+                                                                     float gamma, Segments sg) {
+  const int hb = heavy_blocks(sg);
+  const int lb = (sg.n_list * kPrimalListLanes + kThreads - 1) / kThreads;
+  const int b = int(blockIdx.x);
+  if (b < hb + lb) {
+    if (b < hb)
+      primal_group<kHeavyLanes>(v, u, ubar, p, tau, soff, samp, gamma, sg.heavy, sg.n_heavy, b);
+    else
+      primal_group<kPrimalListLanes>(v, u, ubar, p, tau, soff, samp, gamma, sg.list, sg.n_list,
+                                     b - hb);
     return;
   }
-  bool listed;
-  const int64_t l = segment_leaf(sg, v.n, &listed);
-  if (l < 0) return;
-  // every load that does not depend on another is issued before any branch
+  const int lbase = hb + lb;
+  // light path: one leaf per thread, single entries only; every load that does
+  // not depend on another is issued before any branch
+  const int64_t l = int64_t(b - lbase) * kThreads + threadIdx.x;
+  if (l >= v.n) return;
   int32_t e[6];
 #pragma unroll
   for (int f = 0; f < 6; ++f) e[f] = v.nbr[int64_t(f) * v.stride + l];
@@ -402,38 +313,28 @@ __global__ void __launch_bounds__(kThreads, kIterMinBlocks) k_primal(View v, flo
   const float ul = u[l];
   const uint32_t o = soff[l];
   const int W = int(soff[l + 1] - o);
-  float dv;
-  if (!listed) {
-    // light path: single entries only; a list leaf's lane gathers its own
-    // p (harmless) and writes nothing (its list thread does)
-    float pn[3];
+  // a list leaf's lane gathers its own p (harmless) and writes nothing
+  float pn[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
-      pn[d] = p[int64_t(d) * v.stride + (e[3 + d] >= 0 ? entry_idx(e[3 + d]) : uint32_t(l))];
-    dv = 0.0f;
+  for (int d = 0; d < 3; ++d)
+    pn[d] = p[int64_t(d) * v.stride + (e[3 + d] >= 0 ? entry_idx(e[3 + d]) : uint32_t(l))];
+  float dv = 0.0f;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const float hm = edge_f(v.D, e[d] >= 0 ? entry_level(e[d]) : lev);
-      dv += (e[d] >= 0 ? inv_delta(h, hm) : 0.0f) * q[d];
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      // same or coarser n: (h_n^3 / h^3) (h / h_n)^2 / Delta = (h_n / h) / Delta
-      const float hn = edge_f(v.D, e[3 + d] >= 0 ? entry_level(e[3 + d]) : lev);
-      dv -= e[3 + d] >= 0 ? (hn / h) * inv_delta(h, hn) * pn[d] : 0.0f;
-    }
-    bool any = false;
-#pragma unroll
-    for (int f = 0; f < 6; ++f) any |= is_list(e[f]);
-    if (any) return;
-  } else {
-    dv = divergence(v, p, l, h, e, q);
+  for (int d = 0; d < 3; ++d) {
+    const float hm = edge_f(v.D, e[d] >= 0 ? entry_level(e[d]) : lev);
+    dv += (e[d] >= 0 ? inv_delta(h, hm) : 0.0f) * q[d];
   }
-  const float x = ul + tl * dv;
-  const float t = tl / (float(W) + gamma);
-  const float un = fminf(fmaxf(prox_l1(samp + o, W, x, t), -1.0f), 1.0f);
-  u[l] = un;
-  ubar[l] = 2.0f * un - ul;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    // same or coarser n: (h_n^3 / h^3) (h / h_n)^2 / Delta = (h_n / h) / Delta
+    const float hn = edge_f(v.D, e[3 + d] >= 0 ? entry_level(e[3 + d]) : lev);
+    dv -= e[3 + d] >= 0 ? (hn / h) * inv_delta(h, hn) * pn[d] : 0.0f;
+  }
+  bool any = false;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) any |= is_list(e[f]);
+  if (any) return;
+  primal_finish(u, ubar, l, ul, tl, dv, o, W, samp, gamma);
 }
 
 // ---------------------------------------------------------------------------
@@ -517,20 +418,41 @@ __device__ __forceinline__ void leaf_terms(const uint32_t* __restrict__ soff,
   // With the samples sorted, sum_k |x - f_k| = x (2 m - W) + sum_k f_k - 2 sum_{k<m} f_k for
   // any m splitting them into f_k <= x (k < m) and f_k >= x (k >= m).  One pass gives
   // the total and the two prefix sums (m = #{f_k < u} for the primal term, m = mx for the
-  // dual term), so each sample costs one float64 addition.
-  double tot = 0.0, su = 0.0, sx = 0.0;
+  // dual term).  The running sum is a float32 pair (hi, lo) updated by Knuth's
+  // error-free TwoSum, so it carries about 48 bits: on GB300's narrow FP64 pipe
+  // this keeps the per-sample work off it, and the prefix sums reach float64 with
+  // a relative error near 2^-48, far below the energy's tolerance.
+  const float ulf = float(ul);
+  float th = 0.0f, tl = 0.0f, uh = 0.0f, ulo = 0.0f, xh = 0.0f, xl = 0.0f;
   int mu = W;
   for (int k = 0; k < W; ++k) {
-    const double f = double(load_sample(samp, o + k));
-    if (mu == W && !(f < ul)) {
+    const float f = load_sample(samp, o + k);
+    if (mu == W && !(f < ulf)) {
       mu = k;
-      su = tot;
+      uh = th;
+      ulo = tl;
     }
-    if (k == mx) sx = tot;
-    tot += f;
+    if (k == mx) {
+      xh = th;
+      xl = tl;
+    }
+    const float sum = __fadd_rn(th, f);
+    const float bv = __fsub_rn(sum, th);
+    const float err = __fadd_rn(__fsub_rn(th, __fsub_rn(sum, bv)), __fsub_rn(f, bv));
+    th = sum;
+    tl = __fadd_rn(tl, err);
   }
-  if (mu == W) su = tot;
-  if (mx == W) sx = tot;
+  if (mu == W) {
+    uh = th;
+    ulo = tl;
+  }
+  if (mx == W) {
+    xh = th;
+    xl = tl;
+  }
+  const double tot = double(th) + double(tl);
+  const double su = double(uh) + double(ulo);
+  const double sx = double(xh) + double(xl);
   const double data = ul * double(2 * mu - W) + tot - 2.0 * su;
   const double dd = xs * double(2 * mx - W) + tot - 2.0 * sx;
   *sp += vol * (rc * data + lambda * sqrt(g2));
@@ -646,15 +568,16 @@ inline unsigned blocks_for(int64_t n, int threads) { return unsigned((n + thread
 
 }  // namespace
 
-inline unsigned grid_of(int64_t n, const Segments& sg) {
-  return blocks_for(n, kThreads) + blocks_for(sg.n_list, kThreads) + unsigned(sg.n_heavy);
+inline unsigned grid_of(int64_t n, const Segments& sg, int list_lanes) {
+  return blocks_for(n, kThreads) + blocks_for(int64_t(sg.n_list) * list_lanes, kThreads) +
+         unsigned(heavy_blocks(sg));
 }
 
 cudaError_t launch_dual(View v, const float* ubar, float* p, const float* sigma, float lambda,
                         LeafSets ls, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
   const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
-  k_dual<false><<<grid_of(v.n, sg), kThreads, 0, s>>>(v, ubar, p, sigma, lambda, sg, 0.0f);
+  k_dual<false><<<grid_of(v.n, sg, kDualListLanes), kThreads, 0, s>>>(v, ubar, p, sigma, lambda, sg, 0.0f);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -663,7 +586,7 @@ cudaError_t launch_dual_init(View v, const float* u, float* p, float lambda, flo
                              cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
   const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
-  k_dual<true><<<grid_of(v.n, sg), kThreads, 0, s>>>(v, u, p, nullptr, lambda, sg, g0);
+  k_dual<true><<<grid_of(v.n, sg, kDualListLanes), kThreads, 0, s>>>(v, u, p, nullptr, lambda, sg, g0);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -673,7 +596,7 @@ cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const f
                           LeafSets ls, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
   const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
-  const unsigned nb = grid_of(v.n, sg);
+  const unsigned nb = grid_of(v.n, sg, kPrimalListLanes);
   if (fp16)
     k_primal<__half><<<nb, kThreads, 0, s>>>(v, u, ubar, p, tau, soff,
                                              reinterpret_cast<const __half*>(samp), gamma, sg);

