@@ -258,7 +258,7 @@ class Clocks:
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("solve.cu", "ofu_internal.cuh"):
+    for f in ("solve.cu", "stencil.cuh", "ofu_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1608_07411_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -598,6 +598,84 @@ def descent_line(a, scene, of, torch, dev, flush, iters=100):
             "energy_after": P, "schedule": "eps 1e-3, xi 0.1 halved every 20 (no split/join)"}
 
 
+def mesh_line(of, torch, dev, big_scene=None):
+    """Marching cubes (Sec. 3.3) and the synthetic-sphere accuracy (Sec. 4):
+    the sphere workload fused adaptively and fully refined (every leaf at
+    D_max, no split/join), both meshed; vertex distances to the analytic
+    surface r = 0.4, and from each adaptive vertex to the nearest vertex of the
+    fully refined mesh (the paper compares its octree result with the dense
+    one).  Then the extraction time on a large scan."""
+    from scipy.spatial import cKDTree
+
+    from paper_1608_07411_gb300.scenes import make_scene
+    sc = make_scene("sphere", 0)
+    g = Gpu(sc, of, torch, dev)
+    out = {"workload": "sphere: r=0.4, 8 views 160x120, D_max 6, 200 iterations, split/join every 10",
+           "voxel_mm": 1e3 * sc.extent / (1 << sc.max_depth)}
+    meshes = {}
+    for name, kw in (("adaptive", {}), ("fully_refined", dict(spread_tau=-1.0, tau_split=2.0, tau_join=2.0))):
+        p = of.params_for(sc)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        c = of.ofu_create_octree(p, g.stream.cuda_stream)
+        g.integrate(c)
+        of.ofu_solve(c, sc.iters, 0 if kw else sc.restructure_every, 0, 0.0)
+        nv, nt = of.ofu_extract_mesh(c)
+        V = np.empty((nv, 3), np.float32)
+        T = np.empty((nt, 3), np.int32)
+        of.ofu_extract_mesh(c, V, nv, T, nt)
+        meshes[name] = V.astype(np.float64)
+        d = np.abs(np.linalg.norm(V.astype(np.float64), axis=1) - 0.4)
+        out[name] = {"leaves": of.ofu_num_leaves(c), "vertices": nv, "triangles": nt,
+                     "dist_to_sphere_mm_mean": 1e3 * float(d.mean()), "dist_to_sphere_mm_std": 1e3 * float(d.std()),
+                     "dist_to_sphere_mm_max": 1e3 * float(d.max())}
+        of.ofu_destroy(c)
+    dd, _ = cKDTree(meshes["fully_refined"]).query(meshes["adaptive"])
+    out["adaptive_to_fully_refined_mm"] = {"mean": 1e3 * float(dd.mean()), "std": 1e3 * float(dd.std())}
+    if big_scene is not None:
+        gb = Gpu(big_scene, of, torch, dev)
+        c = gb.ctx(False)
+        gb.integrate(c)
+        of.ofu_extract_mesh(c)   # scratch allocated outside the timing
+        e0 = gb.event()
+        nv, nt = of.ofu_extract_mesh(c)
+        e1 = gb.event()
+        e1.synchronize()
+        out["extraction"] = {"workload": big_scene.name, "finest_voxels": 8 ** big_scene.max_depth,
+                             "vertices": nv, "triangles": nt, "ms_counts_only": e0.elapsed_time(e1)}
+        of.ofu_destroy(c)
+    return out
+
+
+def frame_tree_line(scene, of, torch, dev):
+    """Per-frame TSDF octrees (data_term = 1, Sec. 3.1 / Fig. 4): build time
+    with the construction, Table 1's dense and octree data-term bytes, the
+    device bytes this library keeps, and one solve on tree samples."""
+    g = Gpu(scene, of, torch, dev)
+    p = of.params_for(scene, frame_trees=True)
+    c = of.ofu_create_octree(p, g.stream.cuda_stream)
+    g.integrate(c)   # warm-up (allocations)
+    torch.cuda.synchronize()
+    e0 = g.event()
+    g.integrate(c)
+    e1 = g.event()
+    e1.synchronize()
+    F = scene.depth.shape[0]
+    nodes = np.empty(F, np.int64)
+    dense, octb, devb = of.ofu_data_term_memory(c, nodes)
+    e2 = g.event()
+    done, li, e = of.ofu_solve(c, scene.iters, scene.restructure_every, 0, 0.0)
+    e3 = g.event()
+    e3.synchronize()
+    out = {"workload": scene.name, "frames": F, "integrate_ms_with_trees": e0.elapsed_time(e1),
+           "dense_MB": dense / 2 ** 20, "octree_MB": octb / 2 ** 20, "device_MB": devb / 2 ** 20,
+           "octree_over_dense": octb / dense, "nodes_per_frame_median": int(np.median(nodes)),
+           "solve_iterations": done, "solve_ms": e2.elapsed_time(e3), "leaf_iterations_per_s": li / (e2.elapsed_time(e3) * 1e-3),
+           "energy": e[0]}
+    of.ofu_destroy(c)
+    return out
+
+
 def quantisation_study(scene, of, torch, dev, checkpoints=(10, 20, 50, 100, 200, 500), sweep_iters=200):
     """Eq. 7 and Sec. 4.2 (Fig. 10 / 11) on the GPU: the quantisation error
     between the adaptive solve (split/join every R iterations) and a fully
@@ -765,6 +843,13 @@ def main():
             make_scene("torus_box", a.seed)
         study = quantisation_study(sscene, of, torch, dev)
 
+    mesh = frames_ = None
+    if rank == 0 and not a.no_study:
+        mesh = mesh_line(of, torch, dev, scene)
+        fscene = sec_scene if sec_scene is not None and sec_scene.name == "torus_box" else \
+            make_scene("torus_box", a.seed)
+        frames_ = frame_tree_line(fscene, of, torch, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         r = cpu_rate(scene, a.cpu_seconds)
@@ -792,7 +877,7 @@ def main():
             "roofline": roofline(res, scene.name), "clocks": clk, "cpu_baseline": cpu,
             "iterate_only": res["iterate_only"], "construction": res["construction"],
             "time_to_energy": tte, "precision": prec, "second_workload": second,
-            "quantisation_study": study, "descent": desc,
+            "quantisation_study": study, "descent": desc, "mesh": mesh, "frame_trees": frames_,
         }
         print(json.dumps(line), flush=True)
     if dist:
