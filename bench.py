@@ -119,7 +119,6 @@ def oracle_crop(scene):
 def _oracle_worker(args):
     """Runs the oracle on a crop for `seconds` (one host process)."""
     crop, seconds = args
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle import solver
     st = solver.initial_state(crop)
     it, t0 = 0, time.perf_counter()
@@ -153,7 +152,19 @@ def cpu_rate(scene, seconds):
     cores = os.cpu_count() or 1
     allc = None
     if cores > 1:
-        with mp.get_context("spawn").Pool(cores) as pool:
+        # one BLAS / OpenMP thread per process (children inherit the environment)
+        names = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {k: os.environ.get(k) for k in names}
+        os.environ.update({k: "1" for k in names})
+        try:
+            pool = mp.get_context("spawn").Pool(cores)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        with pool:
             res = pool.map(_oracle_worker, [(crop, seconds)] * cores)
         allc = sum(w / t for w, t in res)
     return {"one_core": one, "all_cores": allc, "cores": cores, "leaves": len(st.keys),

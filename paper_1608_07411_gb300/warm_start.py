@@ -47,6 +47,9 @@ def init_params(seed: int) -> np.ndarray:
     return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
 
 
+_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
 def _render(args):
     name, seed = args
     return make_scene(name, seed)
@@ -57,7 +60,19 @@ def scenes(name, seeds, workers=None):
     import multiprocessing as mp
     workers = workers or max(1, min(len(seeds), (os.cpu_count() or 2) - 1))
     ctx = mp.get_context("spawn")
-    with ctx.Pool(workers) as pool:
+    # one BLAS / OpenMP thread per worker (children inherit the environment at
+    # spawn; many workers with a thread per core each would oversubscribe)
+    saved = {k: os.environ.get(k) for k in _THREAD_VARS}
+    os.environ.update({k: "1" for k in _THREAD_VARS})
+    try:
+        pool = ctx.Pool(workers)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    with pool:
         for sc in pool.imap(_render, [(name, s) for s in seeds]):
             yield sc
 

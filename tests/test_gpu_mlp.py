@@ -163,3 +163,25 @@ def test_trained_warm_start_gains():
     print("energy per window: plain", plain, "warm", warm, "untrained", raw)
     assert warm[0] < plain[0] < raw[0]
     assert np.all(warm[1:] < plain[1:])
+
+
+def test_training_protocol_small():
+    """The config-5 protocol end to end at a small size: targets converged to a
+    relative gap of 1e-5 on the constructed structure, a few hundred Adam
+    steps, then the held-out evaluation of every form against the plain
+    solver's converged energy (split/join during the refinement iterations,
+    then the structure kept)."""
+    from paper_1608_07411_gb300 import warm_start
+    scans = [make_scene("torus_box", warm_start.TRAIN_SEED0 + k, frames=8, width=128, height=96,
+                        max_depth=6) for k in range(3)]
+    params, losses = warm_start.train(3, 4000, 300, 8192, 2e-3, 0, gap_tol=1e-5, rows_per_scan=6000,
+                                      scan_iter=iter(scans), log=lambda *_: None)
+    assert params.shape == (of.ofu_mlp_num_params(),) and np.all(np.isfinite(params))
+    assert losses[-1][1] < 0.5 * losses[0][1]
+    held = make_scene("at_scale", 1000, frames=12, width=128, height=96, max_depth=6)
+    rows = warm_start.evaluate(params, [held], torch, log=lambda *_: None)
+    r = rows[0]
+    assert r["converged"] and r["seed"] == 1000
+    for form in ("plain_f32", "f16_samples", "f32_warm_start", "f16_warm_start"):
+        assert r[form]["iters"] > 0 and r[form]["ms"] > 0
+    assert r["plain_f32"]["reached"]
