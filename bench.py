@@ -839,6 +839,20 @@ def main():
                   "samples_initial": r2["samples_initial"], "iterate_only": r2["iterate_only"],
                   "roofline": roofline(r2, sec_scene.name), "construction": r2["construction"]}
 
+    fp16_step = None
+    if not a.fp16 and not a.no_precision and rank == 0:
+        # the same protocol with float16 samples (config 4's bandwidth comparison on this scan)
+        r16 = measure(a, scene, of, torch, dev, flush, None, True, with_e2e=False)
+        rf16 = roofline(r16, scene.name)
+        fp16_step = {"samples": "float16", "value": r16["value"], "unit": METRIC,
+                     "ms_per_step": r16["ms_per_step"], "iterations": r16["iterations"],
+                     "rel_gap": r16["rel_gap"], "gap_reached": r16["gap_reached"],
+                     "final_energy": r16["final_energy"],
+                     "primal_kernel": {"achieved_GB_s": rf16["achieved"] if rf16["kernel"] == "k_primal"
+                                       else rf16["other"]["achieved"],
+                                       "avg_launch_us": rf16["avg_launch_us"] if rf16["kernel"] == "k_primal"
+                                       else rf16["other"]["avg_launch_us"]},
+                     "iterate_only": r16["iterate_only"]["value"]}
     tte = None if a.no_tte or rank != 0 else time_to_energy(a, scene, of, torch, dev)
     desc = [descent_line(a, sc, of, torch, dev, flush) for sc in (scene, sec_scene) if sc is not None] \
         if rank == 0 and not a.no_descent else None
@@ -887,7 +901,7 @@ def main():
             "e2e": res["e2e"], "gpu_launches": int(res["gpu_launches"]),
             "roofline": roofline(res, scene.name), "clocks": clk, "cpu_baseline": cpu,
             "iterate_only": res["iterate_only"], "construction": res["construction"],
-            "time_to_energy": tte, "precision": prec, "second_workload": second,
+            "time_to_energy": tte, "precision": prec, "fp16_step": fp16_step, "second_workload": second,
             "quantisation_study": study, "descent": desc, "mesh": mesh, "frame_trees": frames_,
         }
         print(json.dumps(line), flush=True)

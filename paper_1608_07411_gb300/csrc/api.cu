@@ -876,8 +876,7 @@ ofu_status ofu_energy(ofu_ctx* ctx, double* primal, double* dual, double* gap) {
   ST(ensure(ctx, B_PART, energy_tmp_bytes(ctx->n) / sizeof(double) + 4, &part));
   small = part + energy_tmp_bytes(ctx->n) / sizeof(double);
   CU(launch_energy(view_of(ctx), L.u, L.p, L.soff, ctx->samp[ctx->cur], ctx->prm.sample_fp16 != 0,
-                   ctx->prm.lambda, ctx->prm.gamma, ctx->heavy + ctx->heavy_cap, ctx->n_heavy_primal,
-                   part, small, ctx->stream));
+                   ctx->prm.lambda, ctx->prm.gamma, primal_sets(ctx), part, small, ctx->stream));
   double h[3];
   ST(read_back(ctx, small, 3 * sizeof(double), h));
   if (primal) *primal = h[0];
@@ -1092,7 +1091,7 @@ ofu_status ofu_energy_static(ofu_ctx* ctx, double* out3) {
   Leaves& L = ctx->L[ctx->cur];
   CU(launch_energy_static(view_of(ctx), L.u, L.p, L.soff, ctx->samp[ctx->cur],
                           ctx->prm.sample_fp16 != 0, ctx->prm.lambda, ctx->prm.gamma,
-                          ctx->heavy + ctx->heavy_cap, ctx->n_heavy_primal, scratch, ctx->stream));
+                          primal_sets(ctx), scratch, ctx->stream));
   CU(cudaMemcpyAsync(out3, scratch + energy_static_result_offset(), 3 * sizeof(double),
                      cudaMemcpyDefault, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));

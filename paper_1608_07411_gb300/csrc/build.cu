@@ -510,6 +510,12 @@ __global__ void __launch_bounds__(256) k_leaf_fill(
 
 constexpr uint32_t kSmallFill = 64;
 
+// Leaves of more voxels than this are written by the whole grid together
+// (a few coarse leaves can hold a third of the map).
+constexpr uint64_t kHugeFill = uint64_t(1) << 18;
+
+// nbig[0] counts the queued big leaves (from the front of `big`), nbig[1]
+// the huge ones (from the back).
 __global__ void k_map_small(const uint64_t* __restrict__ key, const uint8_t* __restrict__ level,
                             int64_t n, int D, uint32_t* __restrict__ map, uint32_t* __restrict__ big,
                             unsigned long long* __restrict__ nbig) {
@@ -525,8 +531,26 @@ __global__ void k_map_small(const uint64_t* __restrict__ key, const uint8_t* __r
     } else {
       map[k] = uint32_t(l);
     }
+  } else if (h3 > kHugeFill) {
+    big[n - 1 - int64_t(atomicAdd(nbig + 1, 1ull))] = uint32_t(l);
   } else {
     big[atomicAdd(nbig, 1ull)] = uint32_t(l);
+  }
+}
+
+// The huge leaves, each striped over every thread of the grid.
+__global__ void k_map_huge(const uint64_t* __restrict__ key, const uint8_t* __restrict__ level,
+                           const uint32_t* __restrict__ big, int64_t n,
+                           const unsigned long long* __restrict__ nbig, int D,
+                           uint32_t* __restrict__ map) {
+  const unsigned long long nh = nbig[1];
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (unsigned long long b = 0; b < nh; ++b) {
+    const uint32_t l = big[n - 1 - int64_t(b)];
+    const uint64_t h34 = (uint64_t(1) << (3 * (D - level[l]))) / 4;
+    const uint4 w = make_uint4(l, l, l, l);
+    uint4* m4 = reinterpret_cast<uint4*>(map + key[l]);
+    for (uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < h34; j += stride) m4[j] = w;
   }
 }
 
@@ -1629,11 +1653,13 @@ cudaError_t launch_emit(View v, const float* u, const float* p, const uint64_t* 
 cudaError_t launch_map(const uint64_t* key, const uint8_t* level, int64_t n, int D, uint32_t* map,
                        uint32_t* big, unsigned long long* nbig, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(nbig, 0, sizeof(unsigned long long), s);
+  cudaError_t e = cudaMemsetAsync(nbig, 0, 2 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   k_map_small<<<blocks_for(n, 256), 256, 0, s>>>(key, level, n, D, map, big, nbig);
   count_launches(1);
   k_map_big<<<dim3(16, unsigned(sm_count() * 2)), 256, 0, s>>>(key, level, big, nbig, D, map);
+  count_launches(1);
+  k_map_huge<<<unsigned(sm_count() * 4), 256, 0, s>>>(key, level, big, n, nbig, D, map);
   count_launches(1);
   return cudaGetLastError();
 }

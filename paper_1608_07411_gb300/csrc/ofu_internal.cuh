@@ -407,7 +407,8 @@ cudaError_t launch_emit(View v, const float* u, const float* p, const uint64_t* 
                         const int8_t* join_level, uint64_t* nkey, uint8_t* nlevel, float* nu,
                         float* nubar, float* np_, int64_t nstride, int32_t* src, int32_t* fwd,
                         uint32_t* big, unsigned long long* nbig, cudaStream_t s);
-// Voxel -> leaf map of a structure (big: scratch of n entries, nbig: counter).
+// Voxel -> leaf map of a structure (big: scratch of n entries, nbig: two
+// counters, of the big and of the huge leaves).
 cudaError_t launch_map(const uint64_t* key, const uint8_t* level, int64_t n, int D, uint32_t* map,
                        uint32_t* big, unsigned long long* nbig, cudaStream_t s);
 cudaError_t launch_new_list(const int32_t* src, int64_t n, uint32_t* list,
@@ -430,17 +431,15 @@ cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const f
                           LeafSets ls, cudaStream_t s);
 size_t energy_tmp_bytes(int64_t n);
 cudaError_t launch_energy(View v, const float* u, const float* p, const uint32_t* soff,
-                          const void* samp, bool fp16, double lambda, double gamma,
-                          const uint32_t* heavy, int n_heavy, double* partial, double* out3,
-                          cudaStream_t s);
+                          const void* samp, bool fp16, double lambda, double gamma, LeafSets ls,
+                          double* partial, double* out3, cudaStream_t s);
 
 // Energy with its scratch in a file-scope device array (solve.cu).
 int64_t energy_static_max_leaves();
 cudaError_t energy_static_scratch(double** ptr);
 cudaError_t launch_energy_static(View v, const float* u, const float* p, const uint32_t* soff,
                                  const void* samp, bool fp16, double lambda, double gamma,
-                                 const uint32_t* heavy, int n_heavy, double* scratch,
-                                 cudaStream_t s);
+                                 LeafSets ls, double* scratch, cudaStream_t s);
 int energy_static_result_offset();
 
 // Warm-start network (mlp.cu).

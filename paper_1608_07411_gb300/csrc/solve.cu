@@ -10,6 +10,8 @@
 // divergence gathers from the -face lists and nothing is scattered.
 #include <math_constants.h>
 
+#include <algorithm>
+
 #include "stencil.cuh"
 
 namespace ofu {
@@ -368,38 +370,6 @@ __device__ __forceinline__ double face_weight(int a, int b) {
   return b < a ? inv_delta * pow2d(2 * (b - a)) : inv_delta;
 }
 
-// Neighbour sums of one leaf's energy terms over one face's entries, split
-// over `nthr` threads starting at `t0` (1 and 0 for a thread, the block for a
-// heavy leaf): for a +face the gradient component and its coefficient sum,
-// for a -face the divergence contribution.
-__device__ __forceinline__ void face_terms(const View& v, const float* __restrict__ u,
-                                           const float* __restrict__ p, int64_t l, int a, double ul,
-                                           int face, int t0, int nthr, double* g, double* coef,
-                                           double* dvm) {
-  const int32_t e = v.nbr[int64_t(face) * v.stride + l];
-  if (e == kEmpty) return;
-  const int32_t* lst = &e;
-  int cnt = 1;
-  if (e < 0) {
-    cnt = v.ovf[list_start(e)];
-    lst = v.ovf + list_start(e) + 1;
-  }
-  const int d = face % 3;
-  for (int k = t0; k < cnt; k += nthr) {
-    const int32_t f = lst[k];
-    const int b = v.D - entry_level(f);
-    if (face < 3) {
-      const double w = face_weight(a, b);
-      *g += w * (double(u[entry_idx(f)]) - ul);
-      *coef += w;
-    } else {
-      // (h_n^3 / h^3) alpha_nl / Delta
-      const double w = face_weight(b, a) * pow2d(3 * (b - a));
-      *dvm += w * double(p[int64_t(d) * v.stride + entry_idx(f)]);
-    }
-  }
-}
-
 // Primal and dual terms of leaf l from its gradient (g2 = |g|^2) and div p.
 template <typename T>
 __device__ __forceinline__ void leaf_terms(const uint32_t* __restrict__ soff,
@@ -470,58 +440,108 @@ __device__ __forceinline__ double block_sum_d(double x, double* red) {
   return t;
 }
 
-// Blocks [0, n_heavy_blocks) sum the heavy leaves (one leaf at a time per
-// block, list entries split over the block); the other blocks the light
-// leaves, one per thread.  Each block writes its (primal, dual) partial.
+// Sum over the G lanes of a group of one double (groups aligned in the warp;
+// every lane of the warp takes part).
+template <int G>
+__device__ __forceinline__ double group_sum_d(double x) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+
+// Energy terms of leaf l, its slots spread over a group of G lanes: the
+// float64 gradient of u (+faces) and divergence of p (both sides), reduced
+// over the group; lane 0 adds the leaf's primal and dual terms to sp, sd
+// when `valid`.
+template <int G, typename T>
+__device__ __forceinline__ void leaf_energy(const View& v, const float* __restrict__ u,
+                                            const float* __restrict__ p,
+                                            const uint32_t* __restrict__ soff,
+                                            const T* __restrict__ samp, double lambda, double gamma,
+                                            int64_t l, int lane, bool valid, double* sp, double* sd) {
+  int32_t e[6];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) e[f] = v.nbr[int64_t(f) * v.stride + l];
+  const int a = v.D - v.level[l];
+  const double ul = double(u[l]);
+  double g0 = 0.0, g1 = 0.0, g2 = 0.0, c0 = 0.0, c1 = 0.0, c2 = 0.0, m0 = 0.0, m1 = 0.0, m2 = 0.0;
+  for_each_slot<6, 2>(v, e, lane, G, [&](int f, int32_t ent) {
+    const int b = v.D - entry_level(ent);
+    if (f < 3) {
+      const double w = face_weight(a, b);
+      const double t = w * (double(u[entry_idx(ent)]) - ul);
+      g0 += f == 0 ? t : 0.0;
+      g1 += f == 1 ? t : 0.0;
+      g2 += f == 2 ? t : 0.0;
+      c0 += f == 0 ? w : 0.0;
+      c1 += f == 1 ? w : 0.0;
+      c2 += f == 2 ? w : 0.0;
+    } else {
+      // (h_n^3 / h^3) alpha_nl / Delta
+      const double w = face_weight(b, a) * pow2d(3 * (b - a));
+      const double t = w * double(p[int64_t(f - 3) * v.stride + entry_idx(ent)]);
+      m0 += f == 3 ? t : 0.0;
+      m1 += f == 4 ? t : 0.0;
+      m2 += f == 5 ? t : 0.0;
+    }
+  });
+  g0 = group_sum_d<G>(g0);
+  g1 = group_sum_d<G>(g1);
+  g2 = group_sum_d<G>(g2);
+  c0 = group_sum_d<G>(c0);
+  c1 = group_sum_d<G>(c1);
+  c2 = group_sum_d<G>(c2);
+  m0 = group_sum_d<G>(m0);
+  m1 = group_sum_d<G>(m1);
+  m2 = group_sum_d<G>(m2);
+  if (lane != 0 || !valid) return;
+  const double dv = (c0 * double(p[l]) - m0) + (c1 * double(p[v.stride + l]) - m1) +
+                    (c2 * double(p[2 * v.stride + l]) - m2);
+  leaf_terms(soff, samp, l, a, ul, g0 * g0 + g1 * g1 + g2 * g2, dv, lambda, gamma, sp, sd);
+}
+
+constexpr int kEnergyListLanes = 4;
+
+// Launch layout: hb blocks of heavy leaves (a warp per leaf, strided over
+// the heavy set), lb blocks of list leaves (kEnergyListLanes lanes per leaf,
+// strided over the list set), then light leaves (a thread each, strided over
+// all leaves, skipping those with a finer-neighbour list).  Each block writes
+// its (primal, dual) partial; all sums are in a fixed order.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_energy(View v, const float* __restrict__ u,
-                                                     const float* __restrict__ p,
-                                                     const uint32_t* __restrict__ soff,
-                                                     const T* __restrict__ samp, double lambda,
-                                                     double gamma, const uint32_t* __restrict__ heavy,
-                                                     int n_heavy, int n_heavy_blocks,
-                                                     double* __restrict__ partial) {
+__global__ void __launch_bounds__(kThreads, 4) k_energy(View v, const float* __restrict__ u,
+                                                        const float* __restrict__ p,
+                                                        const uint32_t* __restrict__ soff,
+                                                        const T* __restrict__ samp, double lambda,
+                                                        double gamma, Segments sg, int hb, int lb,
+                                                        double* __restrict__ partial) {
   __shared__ double red[kThreads / 32];
   double sp = 0.0, sd = 0.0;
-  if (int(blockIdx.x) < n_heavy_blocks) {
-    for (int q = blockIdx.x; q < n_heavy; q += n_heavy_blocks) {
-      const int64_t l = heavy[q];
-      const int a = v.D - v.level[l];
-      const double ul = double(u[l]);
-      double g2 = 0.0, dv = 0.0;
-      for (int d = 0; d < 3; ++d) {
-        double g = 0.0, coef = 0.0, dvm = 0.0;
-        face_terms(v, u, p, l, a, ul, d, threadIdx.x, kThreads, &g, &coef, &dvm);
-        face_terms(v, u, p, l, a, ul, 3 + d, threadIdx.x, kThreads, &g, &coef, &dvm);
-        g = block_sum_d(g, red);
-        coef = block_sum_d(coef, red);
-        dvm = block_sum_d(dvm, red);
-        g2 += g * g;
-        dv += coef * double(p[int64_t(d) * v.stride + l]) - dvm;
-      }
-      if (threadIdx.x == 0) leaf_terms(soff, samp, l, a, ul, g2, dv, lambda, gamma, &sp, &sd);
+  const int b = int(blockIdx.x);
+  if (b < hb) {
+    const int w = b * (kThreads / 32) + int(threadIdx.x >> 5), nw = hb * (kThreads / 32);
+    for (int q = w; q < sg.n_heavy; q += nw)
+      leaf_energy<32>(v, u, p, soff, samp, lambda, gamma, sg.heavy[q], int(threadIdx.x & 31), true,
+                      &sp, &sd);
+  } else if (b < hb + lb) {
+    constexpr int G = kEnergyListLanes;
+    const int t = (b - hb) * kThreads + int(threadIdx.x);
+    const int gi = t / G, ng = lb * (kThreads / G);
+    const int rounds = (sg.n_list + ng - 1) / ng;   // the same in every lane
+    for (int r = 0; r < rounds; ++r) {
+      const int q = gi + r * ng;
+      const bool valid = q < sg.n_list;
+      leaf_energy<G>(v, u, p, soff, samp, lambda, gamma, sg.list[valid ? q : sg.n_list - 1], t % G,
+                     valid, &sp, &sd);
     }
   } else {
-    const int nb = int(gridDim.x) - n_heavy_blocks;
-    for (int64_t l = int64_t(blockIdx.x - n_heavy_blocks) * blockDim.x + threadIdx.x; l < v.n;
+    const int nb = int(gridDim.x) - hb - lb;
+    for (int64_t l = int64_t(b - hb - lb) * blockDim.x + threadIdx.x; l < v.n;
          l += int64_t(nb) * blockDim.x) {
-      bool heavy_leaf = false;
-      for (int face = 0; face < 6; ++face) {
-        const int32_t e = v.nbr[int64_t(face) * v.stride + l];
-        heavy_leaf |= is_list(e) && v.ovf[list_start(e)] > kHeavy;
-      }
-      if (heavy_leaf) continue;   // summed by a heavy block
-      const int a = v.D - v.level[l];
-      const double ul = double(u[l]);
-      double g2 = 0.0, dv = 0.0;
-      for (int d = 0; d < 3; ++d) {
-        double g = 0.0, coef = 0.0, dvm = 0.0;
-        face_terms(v, u, p, l, a, ul, d, 0, 1, &g, &coef, &dvm);
-        face_terms(v, u, p, l, a, ul, 3 + d, 0, 1, &g, &coef, &dvm);
-        g2 += g * g;
-        dv += coef * double(p[int64_t(d) * v.stride + l]) - dvm;
-      }
-      leaf_terms(soff, samp, l, a, ul, g2, dv, lambda, gamma, &sp, &sd);
+      bool listed = false;
+#pragma unroll
+      for (int f = 0; f < 6; ++f) listed |= is_list(v.nbr[int64_t(f) * v.stride + l]);
+      if (listed) continue;   // summed by a heavy or list group
+      leaf_energy<1>(v, u, p, soff, samp, lambda, gamma, l, 0, true, &sp, &sd);
     }
   }
   // block partial in a fixed order
@@ -609,26 +629,43 @@ cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const f
 
 size_t energy_tmp_bytes(int64_t) { return size_t(2 * kEnergyBlocks) * sizeof(double); }
 
-// Heavy leaves get min(n_heavy, kEnergyHeavyBlocks) blocks at the front of
-// the grid; light leaves up to kEnergyBlocks - that many.
-constexpr int kEnergyHeavyBlocks = 256;
+// Grid of k_energy: at most 128 blocks of heavy warps and 1024 of list
+// groups (both strided over their sets), then light blocks of up to
+// `per_light_block` leaves each (strided), max_blocks in all.
+struct EnergyLayout {
+  int hb, lb, nb;
+};
+
+inline EnergyLayout energy_layout(int64_t n, const Segments& sg, int64_t per_light_block,
+                                  int max_blocks) {
+  EnergyLayout g;
+  g.hb = int(std::min<int64_t>((int64_t(sg.n_heavy) * 32 + kThreads - 1) / kThreads, 128));
+  g.lb = int(std::min<int64_t>((int64_t(sg.n_list) * kEnergyListLanes + kThreads - 1) / kThreads, 1024));
+  const int64_t want = (n + per_light_block - 1) / per_light_block;
+  const int64_t room = max_blocks - g.hb - g.lb;
+  g.nb = g.hb + g.lb + int(std::max<int64_t>(1, std::min<int64_t>(want, room)));
+  return g;
+}
+
+template <typename T>
+void energy_launch(EnergyLayout g, View v, const float* u, const float* p, const uint32_t* soff,
+                   const void* samp, double lambda, double gamma, Segments sg, double* partial,
+                   cudaStream_t s) {
+  k_energy<T><<<g.nb, kThreads, 0, s>>>(v, u, p, soff, reinterpret_cast<const T*>(samp), lambda,
+                                        gamma, sg, g.hb, g.lb, partial);
+}
 
 cudaError_t launch_energy(View v, const float* u, const float* p, const uint32_t* soff,
-                          const void* samp, bool fp16, double lambda, double gamma,
-                          const uint32_t* heavy, int n_heavy, double* partial, double* out3,
-                          cudaStream_t s) {
-  const int hb = n_heavy < kEnergyHeavyBlocks ? n_heavy : kEnergyHeavyBlocks;
-  const int64_t want = (v.n + kThreads - 1) / kThreads;
-  const int lb = int(want < 1 ? 1 : (want < kEnergyBlocks - hb ? want : kEnergyBlocks - hb));
-  const int nb = hb + lb;
+                          const void* samp, bool fp16, double lambda, double gamma, LeafSets ls,
+                          double* partial, double* out3, cudaStream_t s) {
+  const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
+  const EnergyLayout g = energy_layout(v.n, sg, kThreads, kEnergyBlocks);
   if (fp16)
-    k_energy<__half><<<nb, kThreads, 0, s>>>(v, u, p, soff, reinterpret_cast<const __half*>(samp),
-                                             lambda, gamma, heavy, n_heavy, hb, partial);
+    energy_launch<__half>(g, v, u, p, soff, samp, lambda, gamma, sg, partial, s);
   else
-    k_energy<float><<<nb, kThreads, 0, s>>>(v, u, p, soff, reinterpret_cast<const float*>(samp),
-                                            lambda, gamma, heavy, n_heavy, hb, partial);
+    energy_launch<float>(g, v, u, p, soff, samp, lambda, gamma, sg, partial, s);
   count_launches(1);
-  k_energy_final<<<1, kFinalThreads, 0, s>>>(partial, nb, out3);
+  k_energy_final<<<1, kFinalThreads, 0, s>>>(partial, g.nb, out3);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -664,21 +701,17 @@ cudaError_t energy_static_scratch(double** ptr) {
 
 cudaError_t launch_energy_static(View v, const float* u, const float* p, const uint32_t* soff,
                                  const void* samp, bool fp16, double lambda, double gamma,
-                                 const uint32_t* heavy, int n_heavy, double* scratch,
-                                 cudaStream_t s) {
+                                 LeafSets ls, double* scratch, cudaStream_t s) {
   const int64_t want = (v.n + kStaticLeavesPerBlock - 1) / kStaticLeavesPerBlock;
   if (want > kStaticEnergyBlocks) return cudaErrorInvalidValue;
-  const int hb = n_heavy < kEnergyHeavyBlocks ? n_heavy : kEnergyHeavyBlocks;
-  const int lb = want < 1 ? 1 : int(want);
-  const int nb = lb + hb <= kStaticEnergyBlocks ? lb + hb : kStaticEnergyBlocks;
+  const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
+  const EnergyLayout g = energy_layout(v.n, sg, kStaticLeavesPerBlock, kStaticEnergyBlocks);
   if (fp16)
-    k_energy<__half><<<nb, kThreads, 0, s>>>(v, u, p, soff, reinterpret_cast<const __half*>(samp),
-                                             lambda, gamma, heavy, n_heavy, hb, scratch);
+    energy_launch<__half>(g, v, u, p, soff, samp, lambda, gamma, sg, scratch, s);
   else
-    k_energy<float><<<nb, kThreads, 0, s>>>(v, u, p, soff, reinterpret_cast<const float*>(samp),
-                                            lambda, gamma, heavy, n_heavy, hb, scratch);
+    energy_launch<float>(g, v, u, p, soff, samp, lambda, gamma, sg, scratch, s);
   count_launches(1);
-  k_energy_final<<<1, kFinalThreads, 0, s>>>(scratch, nb, scratch + 2 * kStaticEnergyBlocks);
+  k_energy_final<<<1, kFinalThreads, 0, s>>>(scratch, g.nb, scratch + 2 * kStaticEnergyBlocks);
   count_launches(1);
   return cudaGetLastError();
 }
