@@ -1361,17 +1361,6 @@ __global__ void k_w_from_soff(const uint32_t* __restrict__ soff, int64_t n, int3
   if (i < n) out[i] = int32_t(soff[i + 1] - soff[i]);
 }
 
-int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
-}
-
 inline unsigned blocks_for(int64_t n, int threads) {
   return unsigned((n + threads - 1) / threads);
 }
@@ -1390,6 +1379,17 @@ int pad_frames(int F) {
 }
 
 }  // namespace
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
 
 // ---------------------------------------------------------------------------
 // launchers

@@ -429,6 +429,8 @@ cudaError_t launch_dual_init(View v, const float* u, float* p, float lambda, flo
 cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const float* tau,
                           const uint32_t* soff, const void* samp, bool fp16, float gamma,
                           LeafSets ls, cudaStream_t s);
+// SMs of the current device (looked up once per process; build.cu).
+int sm_count();
 size_t energy_tmp_bytes(int64_t n);
 cudaError_t launch_energy(View v, const float* u, const float* p, const uint32_t* soff,
                           const void* samp, bool fp16, double lambda, double gamma, LeafSets ls,

@@ -76,6 +76,9 @@ constexpr int kPrimalListLanes = 2;
 constexpr int kHeavyLanes = 32;
 // Slots a lane of the primal step loads per round (registers allow 2 there).
 constexpr int kPrimalSlotBatch = 2;
+// Leaves per thread of the dual and primal steps' light paths.
+constexpr int kDualLightLeaves = 2;
+constexpr int kPrimalLightLeaves = 1;
 
 // Blocks of the heavy segment (kHeavyLanes lanes per heavy leaf).
 __device__ __host__ __forceinline__ int heavy_blocks(const Segments& sg) {
@@ -131,55 +134,48 @@ __global__ void __launch_bounds__(kThreads, kIterMinBlocks) k_dual(View v, const
     return;
   }
   const int lbase = hb + lb;
-  // light path: one leaf per thread, single entries only; every load that does
-  // not depend on another is issued before any branch
-  const int64_t l = int64_t(b - lbase) * kThreads + threadIdx.x;
-  if (l >= v.n) return;
-  const int32_t e[3] = {v.nbr[l], v.nbr[st + l], v.nbr[2 * st + l]};
-  const int lev = v.level[l];
-  const float h = edge_f(v.D, lev);
-  const float ul = ubar[l];
-  const float q[3] = {p[l], p[st + l], p[2 * st + l]};
-  const float sl = INIT ? 0.0f : sigma[l];
-  // a list leaf's lane gathers its own value (harmless) and writes nothing
-  float x[3];
+  // light path: kDualLightLeaves leaves per thread (a block covers that many
+  // runs of kThreads consecutive leaves), single entries only.  All loads of
+  // all of them are issued before any gather, and all gathers before any
+  // arithmetic, so a thread keeps several independent loads in flight.  A
+  // thread past the end re-reads the last leaf and writes nothing; a list
+  // leaf's lane gathers its own value (harmless) and writes nothing.
+  constexpr int K = kDualLightLeaves;
+  const int64_t base = int64_t(b - lbase) * (kThreads * K) + threadIdx.x;
+  int64_t l[K];
+  int32_t e[K][3];
+  int lev[K];
+  float ul[K], q[K][3], sl[K];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) x[d] = ubar[e[d] >= 0 ? entry_idx(e[d]) : uint32_t(l)];
-  float g[3];
+  for (int j = 0; j < K; ++j) {
+    l[j] = base + j * kThreads;
+    const int64_t lc = l[j] < v.n ? l[j] : v.n - 1;
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const float hm = edge_f(v.D, e[d] >= 0 ? entry_level(e[d]) : lev);
-    g[d] = e[d] >= 0 ? (x[d] - ul) * inv_delta(h, hm) : 0.0f;
+    for (int d = 0; d < 3; ++d) e[j][d] = v.nbr[d * st + lc];
+    lev[j] = v.level[lc];
+    ul[j] = ubar[lc];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) q[j][d] = p[d * st + lc];
+    sl[j] = INIT ? 0.0f : sigma[lc];
+    if (l[j] >= v.n) l[j] = -1;
   }
-  if (is_list(e[0]) || is_list(e[1]) || is_list(e[2])) return;
-  dual_finish<INIT>(p, st, l, q, sl, g, lambda, g0);
-}
-
-// Prox of the data term: argmin_x (x - v)^2 / (2 tau) + c sum_k |x - f_k| is
-// the median of {f_k} and {v + t (W - 2k)}_{k=0..W}, t = tau c.  With the
-// samples sorted it is clamp(b_k*, f_(k*-1), f_k*) (0-based f, f_-1 = -inf,
-// f_W = +inf) where k* is the number of k with f_k < b_k = v + t (W - 2k).
-// That predicate holds exactly for a prefix of k (f rises, b falls, and the
-// rounded b_k still falls), so k* is found by bisection in ceil(log2(W + 1))
-// probes.  The last probe that held is f_(k*-1), the last that failed is
-// f_k*, so no sample is loaded twice.
-template <typename T>
-__device__ __forceinline__ float prox_l1(const T* __restrict__ f, int W, float v, float t) {
-  int lo = 0, hi = W;
-  float flo = -CUDART_INF_F, fhi = CUDART_INF_F;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    const float fm = load_sample(f, mid);
-    if (fm < __fmaf_rn(t, float(W - 2 * mid), v)) {
-      lo = mid + 1;
-      flo = fm;
-    } else {
-      hi = mid;
-      fhi = fm;
+  float x[K][3];
+#pragma unroll
+  for (int j = 0; j < K; ++j)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) x[j][d] = ubar[e[j][d] >= 0 ? entry_idx(e[j][d]) : 0u];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const float h = edge_f(v.D, lev[j]);
+    float g[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float hm = edge_f(v.D, e[j][d] >= 0 ? entry_level(e[j][d]) : lev[j]);
+      g[d] = e[j][d] >= 0 ? (x[j][d] - ul[j]) * inv_delta(h, hm) : 0.0f;
     }
+    if (l[j] < 0 || is_list(e[j][0]) || is_list(e[j][1]) || is_list(e[j][2])) continue;
+    dual_finish<INIT>(p, st, l[j], q[j], sl[j], g, lambda, g0);
   }
-  const float b = __fmaf_rn(t, float(W - 2 * lo), v);
-  return fmaxf(flo, fminf(b, fhi));
 }
 
 // Divergence of p at leaf l over its six faces' slots, this lane's share of
@@ -200,12 +196,13 @@ __device__ __forceinline__ float div_share(const View& v, const float* __restric
   return acc;
 }
 
-// The prox of prox_l1 found by a group of G lanes: each round the lanes test
-// G evenly spaced ranks of [lo, hi) and the count of those that hold (a prefix,
-// the predicate being monotone) narrows the range, so a leaf of W samples
-// takes about log_G(W) rounds of independent loads.  k* is the same as the
-// bisection's, hence so is the result, in every lane.  The count is a warp
-// ballot (every lane of the warp takes part in every round).
+// The prox of the data term (described at primal_light) found by a group of
+// G lanes: each round the lanes test G evenly spaced ranks of [lo, hi) and the
+// count of those that hold (a prefix, the predicate being monotone) narrows
+// the range, so a leaf of W samples takes about log_G(W) rounds of
+// independent loads.  k* is the same as the bisection's, hence so is the
+// result, in every lane.  The count is a warp ballot (every lane of the warp
+// takes part in every round).
 template <int G, typename T>
 __device__ __forceinline__ float prox_l1_group(const T* __restrict__ f, int W, float v, float t,
                                                int lane) {
@@ -234,17 +231,6 @@ __device__ __forceinline__ float prox_l1_group(const T* __restrict__ f, int W, f
   const float fhi = lo < W ? load_sample(f, lo) : CUDART_INF_F;
   const float b = __fmaf_rn(t, float(W - 2 * lo), v);
   return fmaxf(flo, fminf(b, fhi));
-}
-
-template <typename T>
-__device__ __forceinline__ void primal_finish(float* __restrict__ u, float* __restrict__ ubar,
-                                              int64_t l, float ul, float tl, float dv, uint32_t o,
-                                              int W, const T* __restrict__ samp, float gamma) {
-  const float x = ul + tl * dv;
-  const float t = tl / (float(W) + gamma);
-  const float un = fminf(fmaxf(prox_l1(samp + o, W, x, t), -1.0f), 1.0f);
-  u[l] = un;
-  ubar[l] = 2.0f * un - ul;
 }
 
 // A primal step of the leaves of a compacted set, G lanes per leaf (layout
@@ -279,6 +265,119 @@ __device__ __forceinline__ void primal_group(const View& v, float* __restrict__ 
   ubar[l] = 2.0f * un - ul;
 }
 
+// Prox of the data term: argmin_x (x - v)^2 / (2 tau) + c sum_k |x - f_k| is
+// the median of {f_k} and {v + t (W - 2k)}_{k=0..W}, t = tau c.  With the
+// samples sorted it is clamp(b_k*, f_(k*-1), f_k*) (0-based f, f_-1 = -inf,
+// f_W = +inf) where k* is the number of k with f_k < b_k = v + t (W - 2k).
+// That predicate holds exactly for a prefix of k (f rises, b falls, and the
+// rounded b_k still falls), so k* is found by bisection in ceil(log2(W + 1))
+// probes (primal_light), or by a group search over G lanes (prox_l1_group).
+// The last probe that held is f_(k*-1), the last that failed is f_k*, so no
+// sample is loaded twice.
+//
+// Primal step of the light path: K leaves per thread (a block covers K runs
+// of kThreads consecutive leaves), single entries only.  The loads of all K
+// leaves are issued before their gathers, and the K bisections of the prox
+// run in lock step, so each round has K independent sample loads in flight.
+// A thread past the end re-reads the last leaf and writes nothing; a list
+// leaf's lane gathers its own p (harmless) and writes nothing.
+template <int K, typename T>
+__device__ __forceinline__ void primal_light(const View& v, float* __restrict__ u,
+                                             float* __restrict__ ubar, const float* __restrict__ p,
+                                             const float* __restrict__ tau,
+                                             const uint32_t* __restrict__ soff,
+                                             const T* __restrict__ samp, float gamma, int b) {
+  const size_t st = size_t(v.stride);
+  const int64_t base = int64_t(b) * (kThreads * K) + threadIdx.x;
+  int64_t l[K];
+  int32_t e[K][6];
+  int lev[K], W[K];
+  float q[K][3], tl[K], ul[K];
+  uint32_t o[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    l[j] = base + j * kThreads;
+    const int64_t lc = l[j] < v.n ? l[j] : v.n - 1;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) e[j][f] = v.nbr[f * st + lc];
+    lev[j] = v.level[lc];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) q[j][d] = p[d * st + lc];
+    tl[j] = tau[lc];
+    ul[j] = u[lc];
+    o[j] = soff[lc];
+    W[j] = int(soff[lc + 1] - o[j]);
+  }
+  float pn[K][3];
+#pragma unroll
+  for (int j = 0; j < K; ++j)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) pn[j][d] = p[d * st + (e[j][3 + d] >= 0 ? entry_idx(e[j][3 + d]) : 0u)];
+  // prox argument x, scaled weight t and the bisection state [lo, hi) per leaf
+  float x[K], t[K], flo[K], fhi[K];
+  int lo[K], hi[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const float h = edge_f(v.D, lev[j]);
+    float dv = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float hm = edge_f(v.D, e[j][d] >= 0 ? entry_level(e[j][d]) : lev[j]);
+      dv += (e[j][d] >= 0 ? inv_delta(h, hm) : 0.0f) * q[j][d];
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      // same or coarser n: (h_n^3 / h^3) (h / h_n)^2 / Delta = (h_n / h) / Delta
+      const float hn = edge_f(v.D, e[j][3 + d] >= 0 ? entry_level(e[j][3 + d]) : lev[j]);
+      dv -= e[j][3 + d] >= 0 ? (hn / h) * inv_delta(h, hn) * pn[j][d] : 0.0f;
+    }
+    bool skip = l[j] >= v.n;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) skip |= is_list(e[j][f]);
+    if (skip) l[j] = -1;
+    x[j] = ul[j] + tl[j] * dv;
+    t[j] = tl[j] / (float(W[j]) + gamma);
+    lo[j] = 0;
+    hi[j] = skip ? 0 : W[j];
+    flo[j] = -CUDART_INF_F;
+    fhi[j] = CUDART_INF_F;
+  }
+  // the bisection for the K leaves at once
+  for (;;) {
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < K; ++j) any |= lo[j] < hi[j];
+    if (!any) break;
+    float fm[K];
+    int mid[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      mid[j] = (lo[j] + hi[j]) >> 1;
+      fm[j] = lo[j] < hi[j] ? load_sample(samp + o[j], mid[j]) : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      if (lo[j] < hi[j]) {
+        if (fm[j] < __fmaf_rn(t[j], float(W[j] - 2 * mid[j]), x[j])) {
+          lo[j] = mid[j] + 1;
+          flo[j] = fm[j];
+        } else {
+          hi[j] = mid[j];
+          fhi[j] = fm[j];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    if (l[j] < 0) continue;
+    const float bk = __fmaf_rn(t[j], float(W[j] - 2 * lo[j]), x[j]);
+    const float un = fminf(fmaxf(fmaxf(flo[j], fminf(bk, fhi[j])), -1.0f), 1.0f);
+    u[l[j]] = un;
+    ubar[l[j]] = 2.0f * un - ul[j];
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads, kIterMinBlocks) k_primal(View v, float* __restrict__ u,
                                                                      float* __restrict__ ubar,
@@ -298,106 +397,168 @@ __global__ void __launch_bounds__(kThreads, kIterMinBlocks) k_primal(View v, flo
                                      b - hb);
     return;
   }
-  const int lbase = hb + lb;
-  // light path: one leaf per thread, single entries only; every load that does
-  // not depend on another is issued before any branch
-  const int64_t l = int64_t(b - lbase) * kThreads + threadIdx.x;
-  if (l >= v.n) return;
-  int32_t e[6];
-#pragma unroll
-  for (int f = 0; f < 6; ++f) e[f] = v.nbr[int64_t(f) * v.stride + l];
-  const int lev = v.level[l];
-  const float h = edge_f(v.D, lev);
-  float q[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) q[d] = p[int64_t(d) * v.stride + l];
-  const float tl = tau[l];
-  const float ul = u[l];
-  const uint32_t o = soff[l];
-  const int W = int(soff[l + 1] - o);
-  // a list leaf's lane gathers its own p (harmless) and writes nothing
-  float pn[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d)
-    pn[d] = p[int64_t(d) * v.stride + (e[3 + d] >= 0 ? entry_idx(e[3 + d]) : uint32_t(l))];
-  float dv = 0.0f;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const float hm = edge_f(v.D, e[d] >= 0 ? entry_level(e[d]) : lev);
-    dv += (e[d] >= 0 ? inv_delta(h, hm) : 0.0f) * q[d];
-  }
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    // same or coarser n: (h_n^3 / h^3) (h / h_n)^2 / Delta = (h_n / h) / Delta
-    const float hn = edge_f(v.D, e[3 + d] >= 0 ? entry_level(e[3 + d]) : lev);
-    dv -= e[3 + d] >= 0 ? (hn / h) * inv_delta(h, hn) * pn[d] : 0.0f;
-  }
-  bool any = false;
-#pragma unroll
-  for (int f = 0; f < 6; ++f) any |= is_list(e[f]);
-  if (any) return;
-  primal_finish(u, ubar, l, ul, tl, dv, o, W, samp, gamma);
+  primal_light<kPrimalLightLeaves>(v, u, ubar, p, tau, soff, samp, gamma, b - (hb + lb));
 }
 
 // ---------------------------------------------------------------------------
-// Energy (float64).  Per leaf, with c = 1 / (W + gamma) and volume h^3:
+// Energy.  Per leaf, with c = 1 / (W + gamma) and volume h^3:
 //   primal  h^3 [c sum_k |u - f_k| + lambda |grad u|]
 //   dual    h^3 min_{x in [-1,1]} [c sum_k |x - f_k| - x div p]
 // The dual minimum of the convex piecewise-linear function sits where its
 // slope c (2k - W) - div p turns non-negative: at f_k for the first such k,
-// at -1 if already for k = 0, at +1 if never.  1 / Delta comes from a table
-// (no division in the neighbour loops); partial sums are per block, then
-// summed by one block in a fixed order, so the result is reproducible.
+// at -1 if already for k = 0, at +1 if never.
+//
+// Precision.  GB300 issues float64 at a small fraction of its float32 rate,
+// so per-leaf float64 arithmetic (about a hundred operations a leaf) made this
+// reduction compute-bound.  The per-leaf terms are therefore evaluated in
+// float-float arithmetic: a value is an unevaluated sum hi + lo of two
+// float32s, kept exact by the error-free transformations TwoSum (Knuth) and
+// TwoProduct (Dekker, with a fused multiply-add), which carries about 44
+// significant bits, near float64's 53 and far below the energy's tolerance.
+// Each thread accumulates its leaves in float-float; the block partials and
+// the final sum are float64 in a fixed order, so the result is reproducible.
 
-// 1 / (1 + 2^d), d = 0..15: 1 / Delta = 2^(1 - min(a, b)) / (1 + 2^|a - b|)
-// for leaves of edges 2^a and 2^b.
-__constant__ double kInvOnePlusPow2[16] = {
-    1.0 / 2.0,     1.0 / 3.0,     1.0 / 5.0,     1.0 / 9.0,     1.0 / 17.0,    1.0 / 33.0,
-    1.0 / 65.0,    1.0 / 129.0,   1.0 / 257.0,   1.0 / 513.0,   1.0 / 1025.0,  1.0 / 2049.0,
-    1.0 / 4097.0,  1.0 / 8193.0,  1.0 / 16385.0, 1.0 / 32769.0};
+// float-float value hi + lo with |lo| <= ulp(hi) (not necessarily rounded)
+struct ff {
+  float hi, lo;
+};
 
-__device__ __forceinline__ double pow2d(int e) {
-  return __longlong_as_double(static_cast<long long>(1023 + e) << 52);   // 2^e, |e| < 1000
+// a + b = s + e exactly (Knuth's TwoSum, no ordering needed)
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
 }
 
-// alpha / Delta for the ordered pair (row leaf of edge exponent a, neighbour
-// of edge exponent b) with alpha = min(1, (2^b / 2^a)^2); exact scalings of a
-// table entry by powers of two.
-__device__ __forceinline__ double face_weight(int a, int b) {
+// a + b = s + e exactly when |a| >= |b| or a = 0 (Dekker's FastTwoSum)
+__device__ __forceinline__ ff ff_fast_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// a b = p + e exactly (barring underflow) with one fused multiply-add
+__device__ __forceinline__ ff ff_two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+  const ff s = ff_two_sum(x.hi, y.hi);
+  return ff_fast_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+
+__device__ __forceinline__ ff ff_neg(ff x) { return {-x.hi, -x.lo}; }
+
+// x 2^k, exact (p2 a power of two, no overflow or underflow)
+__device__ __forceinline__ ff ff_scale(ff x, float p2) { return {x.hi * p2, x.lo * p2}; }
+
+__device__ __forceinline__ ff ff_mul_f(ff x, float b) {
+  const ff p = ff_two_prod(x.hi, b);
+  return ff_fast_sum(p.hi, __fmaf_rn(x.lo, b, p.lo));
+}
+
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+  const ff p = ff_two_prod(x.hi, y.hi);
+  return ff_fast_sum(p.hi, __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo)));
+}
+
+// sqrt(x) for x >= 0: s = sqrt(hi) rounded, then one Newton correction
+// (x - s^2) / (2 s), where hi - s^2 is exact (the two are within a factor 2).
+__device__ __forceinline__ ff ff_sqrt(ff x) {
+  if (!(x.hi > 0.0f)) return {0.0f, 0.0f};
+  const float s = __fsqrt_rn(x.hi);
+  const ff sq = ff_two_prod(s, s);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, sq.hi), sq.lo), x.lo);
+  return ff_fast_sum(s, __fdividef(r, 2.0f * s));
+}
+
+// 1 / x for x > 0: r = 1 / hi rounded, then r + r (1 - x r), where 1 - x r
+// is formed from the exact product.
+__device__ __forceinline__ ff ff_recip(ff x) {
+  const float r = __frcp_rn(x.hi);
+  const ff xr = ff_mul_f(x, r);
+  const float e = __fsub_rn(__fsub_rn(1.0f, xr.hi), xr.lo);
+  return ff_fast_sum(r, __fmul_rn(r, e));
+}
+
+__device__ __forceinline__ ff ff_of(double d) {
+  const float hi = __double2float_rn(d);
+  return {hi, __double2float_rn(d - double(hi))};
+}
+
+__device__ __forceinline__ double ff_double(ff x) { return double(x.hi) + double(x.lo); }
+
+// 2^e as a float, -126 <= e <= 127
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+// 1 / (1 + 2^d), d = 0..15, split into a float pair: 1 / Delta for leaves of
+// edges 2^a and 2^b is 2^(1 - min(a, b)) / (1 + 2^|a - b|).
+constexpr double inv_one_plus_pow2(int d) { return 1.0 / (1.0 + double(1 << d)); }
+constexpr float inv_hi(int d) { return float(inv_one_plus_pow2(d)); }
+constexpr float inv_lo(int d) { return float(inv_one_plus_pow2(d) - double(inv_hi(d))); }
+__constant__ float kInvHi[16] = {inv_hi(0),  inv_hi(1),  inv_hi(2),  inv_hi(3),  inv_hi(4),  inv_hi(5),
+                                 inv_hi(6),  inv_hi(7),  inv_hi(8),  inv_hi(9),  inv_hi(10), inv_hi(11),
+                                 inv_hi(12), inv_hi(13), inv_hi(14), inv_hi(15)};
+__constant__ float kInvLo[16] = {inv_lo(0),  inv_lo(1),  inv_lo(2),  inv_lo(3),  inv_lo(4),  inv_lo(5),
+                                 inv_lo(6),  inv_lo(7),  inv_lo(8),  inv_lo(9),  inv_lo(10), inv_lo(11),
+                                 inv_lo(12), inv_lo(13), inv_lo(14), inv_lo(15)};
+
+// alpha / Delta 2^extra for the ordered pair (row leaf of edge exponent a,
+// neighbour of edge exponent b) with alpha = min(1, (2^b / 2^a)^2): a table
+// pair scaled by a power of two, so exact to the pair's precision.
+__device__ __forceinline__ ff face_weight(int a, int b, int extra) {
   const int lo = a < b ? a : b;
   const int d = a < b ? b - a : a - b;
-  const double inv_delta = kInvOnePlusPow2[d] * pow2d(1 - lo);
-  return b < a ? inv_delta * pow2d(2 * (b - a)) : inv_delta;
+  const float s = pow2f(1 - lo + (b < a ? 2 * (b - a) : 0) + extra);
+  return {kInvHi[d] * s, kInvLo[d] * s};
 }
 
-// Primal and dual terms of leaf l from its gradient (g2 = |g|^2) and div p.
+// +face term of neighbour value um: alpha / Delta (um - ul), and the weight
+__device__ __forceinline__ ff grad_term(int a, int b, float um, float ul, ff* w) {
+  *w = face_weight(a, b, 0);
+  return ff_mul(*w, ff_two_sum(um, -ul));
+}
+
+// -face term of neighbour value pn: (h_n^3 / h^3) alpha_nl / Delta pn
+__device__ __forceinline__ ff div_term(int a, int b, float pn) {
+  return ff_mul_f(face_weight(b, a, 3 * (b - a)), pn);
+}
+
+// Primal and dual terms of leaf l (edge exponent a) from its gradient g, the
+// +face weight sums c and the -face sums m of the divergence, and p(l).
 template <typename T>
 __device__ __forceinline__ void leaf_terms(const uint32_t* __restrict__ soff,
-                                           const T* __restrict__ samp, int64_t l, int a, double ul,
-                                           double g2, double dv, double lambda, double gamma,
-                                           double* sp, double* sd) {
-  const double vol = pow2d(3 * a);
+                                           const T* __restrict__ samp, int64_t l, int a, float ul,
+                                           const ff g[3], const ff c[3], const ff m[3],
+                                           const float pl[3], ff lambda, ff gamma, ff* sp, ff* sd) {
+  const ff g2 = ff_add(ff_add(ff_mul(g[0], g[0]), ff_mul(g[1], g[1])), ff_mul(g[2], g[2]));
+  ff dv = ff_add(ff_mul_f(c[0], pl[0]), ff_neg(m[0]));
+  dv = ff_add(dv, ff_add(ff_mul_f(c[1], pl[1]), ff_neg(m[1])));
+  dv = ff_add(dv, ff_add(ff_mul_f(c[2], pl[2]), ff_neg(m[2])));
   const uint32_t o = soff[l];
   const int W = int(soff[l + 1] - o);
-  const double rc = 1.0 / (double(W) + gamma);
+  const float Wf = float(W);
+  const ff wg = ff_add({Wf, 0.0f}, gamma);
+  const ff rc = ff_recip(wg);
   // dual term: first k with slope c (2k - W) - dv >= 0, i.e. k >= (W + dv / c) / 2;
-  // the minimiser is -1 before the first sample, +1 after the last, else f_(k-1)
-  const double kk = ceil((double(W) + dv * (double(W) + gamma)) * 0.5);
-  const int mx = kk <= 0.0 ? 0 : (kk > double(W) ? W : int(kk) - 1);
-  const double xs = kk <= 0.0 ? -1.0 : (kk > double(W) ? 1.0 : double(load_sample(samp, o + mx)));
+  // the minimiser is -1 before the first sample, +1 after the last, else f_(k-1).
+  // ceil of the pair q = (W + dv (W + gamma)) / 2: ceil(q.hi), plus one when
+  // q.hi is an integer and q.lo > 0 (|q.lo| is below the distance from a
+  // non-integer q.hi to the next integer).
+  const ff q = ff_scale(ff_add({Wf, 0.0f}, ff_mul(dv, wg)), 0.5f);
+  float kk = ceilf(q.hi);
+  if (kk == q.hi && q.lo > 0.0f) kk += 1.0f;
+  const int mx = kk <= 0.0f ? 0 : (kk > Wf ? W : int(kk) - 1);
+  const float xs = kk <= 0.0f ? -1.0f : (kk > Wf ? 1.0f : load_sample(samp, o + mx));
   // With the samples sorted, sum_k |x - f_k| = x (2 m - W) + sum_k f_k - 2 sum_{k<m} f_k for
   // any m splitting them into f_k <= x (k < m) and f_k >= x (k >= m).  One pass gives
-  // the total and the two prefix sums (m = #{f_k < u} for the primal term, m = mx for the
-  // dual term).  The running sum is a float32 pair (hi, lo) updated by Knuth's
-  // error-free TwoSum, so it carries about 48 bits: on GB300's narrow FP64 pipe
-  // this keeps the per-sample work off it, and the prefix sums reach float64 with
-  // a relative error near 2^-48, far below the energy's tolerance.
-  const float ulf = float(ul);
+  // the total and the two prefix sums (m = #{f_k < u} for the primal term, m = mx for
+  // the dual term), each a TwoSum pair.
   float th = 0.0f, tl = 0.0f, uh = 0.0f, ulo = 0.0f, xh = 0.0f, xl = 0.0f;
   int mu = W;
   for (int k = 0; k < W; ++k) {
     const float f = load_sample(samp, o + k);
-    if (mu == W && !(f < ulf)) {
+    if (mu == W && !(f < ul)) {
       mu = k;
       uh = th;
       ulo = tl;
@@ -406,11 +567,9 @@ __device__ __forceinline__ void leaf_terms(const uint32_t* __restrict__ soff,
       xh = th;
       xl = tl;
     }
-    const float sum = __fadd_rn(th, f);
-    const float bv = __fsub_rn(sum, th);
-    const float err = __fadd_rn(__fsub_rn(th, __fsub_rn(sum, bv)), __fsub_rn(f, bv));
-    th = sum;
-    tl = __fadd_rn(tl, err);
+    const ff s = ff_two_sum(th, f);
+    th = s.hi;
+    tl = __fadd_rn(tl, s.lo);
   }
   if (mu == W) {
     uh = th;
@@ -420,13 +579,14 @@ __device__ __forceinline__ void leaf_terms(const uint32_t* __restrict__ soff,
     xh = th;
     xl = tl;
   }
-  const double tot = double(th) + double(tl);
-  const double su = double(uh) + double(ulo);
-  const double sx = double(xh) + double(xl);
-  const double data = ul * double(2 * mu - W) + tot - 2.0 * su;
-  const double dd = xs * double(2 * mx - W) + tot - 2.0 * sx;
-  *sp += vol * (rc * data + lambda * sqrt(g2));
-  *sd += vol * (rc * dd - xs * dv);
+  const ff tot = ff_two_sum(th, tl);
+  const ff data = ff_add(ff_add(ff_two_prod(ul, float(2 * mu - W)), tot),
+                         ff_scale(ff_two_sum(uh, ulo), -2.0f));
+  const ff dd = ff_add(ff_add(ff_two_prod(xs, float(2 * mx - W)), tot),
+                       ff_scale(ff_two_sum(xh, xl), -2.0f));
+  const float vol = pow2f(3 * a);
+  *sp = ff_add(*sp, ff_scale(ff_add(ff_mul(rc, data), ff_mul(lambda, ff_sqrt(g2))), vol));
+  *sd = ff_add(*sd, ff_scale(ff_add(ff_mul(rc, dd), ff_neg(ff_mul_f(dv, xs))), vol));
 }
 
 __device__ __forceinline__ double block_sum_d(double x, double* red) {
@@ -440,64 +600,89 @@ __device__ __forceinline__ double block_sum_d(double x, double* red) {
   return t;
 }
 
-// Sum over the G lanes of a group of one double (groups aligned in the warp;
-// every lane of the warp takes part).
+// Sum over the G lanes of a group of one pair (groups aligned in the warp;
+// every lane of the warp takes part; lane 0's sum is in a fixed order).
 template <int G>
-__device__ __forceinline__ double group_sum_d(double x) {
+__device__ __forceinline__ ff group_sum_ff(ff x) {
 #pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  for (int o = G / 2; o > 0; o >>= 1)
+    x = ff_add(x, ff{__shfl_xor_sync(kFull, x.hi, o), __shfl_xor_sync(kFull, x.lo, o)});
   return x;
 }
 
+// Energy terms of a light leaf l (single entries on every face): the six
+// neighbour values are gathered first (an empty face gathers l's own, unused).
+template <typename T>
+__device__ __forceinline__ void light_energy(const View& v, const float* __restrict__ u,
+                                             const float* __restrict__ p,
+                                             const uint32_t* __restrict__ soff,
+                                             const T* __restrict__ samp, ff lambda, ff gamma,
+                                             int64_t l, const int32_t e[6], ff* sp, ff* sd) {
+  const size_t st = size_t(v.stride);
+  const int a = v.D - v.level[l];
+  const float ul = u[l];
+  const float pl[3] = {p[l], p[st + l], p[2 * st + l]};
+  float x[6];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    x[d] = u[e[d] >= 0 ? entry_idx(e[d]) : uint32_t(l)];
+    x[3 + d] = p[d * st + (e[3 + d] >= 0 ? entry_idx(e[3 + d]) : uint32_t(l))];
+  }
+  ff g[3], c[3], m[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const ff zero{0.0f, 0.0f};
+    ff w;
+    const ff t = grad_term(a, e[d] >= 0 ? v.D - entry_level(e[d]) : a, x[d], ul, &w);
+    g[d] = e[d] >= 0 ? t : zero;
+    c[d] = e[d] >= 0 ? w : zero;
+    const ff s = div_term(a, e[3 + d] >= 0 ? v.D - entry_level(e[3 + d]) : a, x[3 + d]);
+    m[d] = e[3 + d] >= 0 ? s : zero;
+  }
+  leaf_terms(soff, samp, l, a, ul, g, c, m, pl, lambda, gamma, sp, sd);
+}
+
 // Energy terms of leaf l, its slots spread over a group of G lanes: the
-// float64 gradient of u (+faces) and divergence of p (both sides), reduced
-// over the group; lane 0 adds the leaf's primal and dual terms to sp, sd
-// when `valid`.
+// gradient of u (+faces) and divergence of p (both sides), reduced over the
+// group; lane 0 adds the leaf's primal and dual terms to sp, sd when `valid`.
 template <int G, typename T>
-__device__ __forceinline__ void leaf_energy(const View& v, const float* __restrict__ u,
-                                            const float* __restrict__ p,
-                                            const uint32_t* __restrict__ soff,
-                                            const T* __restrict__ samp, double lambda, double gamma,
-                                            int64_t l, int lane, bool valid, double* sp, double* sd) {
+__device__ __forceinline__ void group_energy(const View& v, const float* __restrict__ u,
+                                             const float* __restrict__ p,
+                                             const uint32_t* __restrict__ soff,
+                                             const T* __restrict__ samp, ff lambda, ff gamma,
+                                             int64_t l, int lane, bool valid, ff* sp, ff* sd) {
   int32_t e[6];
 #pragma unroll
   for (int f = 0; f < 6; ++f) e[f] = v.nbr[int64_t(f) * v.stride + l];
   const int a = v.D - v.level[l];
-  const double ul = double(u[l]);
-  double g0 = 0.0, g1 = 0.0, g2 = 0.0, c0 = 0.0, c1 = 0.0, c2 = 0.0, m0 = 0.0, m1 = 0.0, m2 = 0.0;
+  const float ul = u[l];
+  const ff zero{0.0f, 0.0f};
+  ff g[3] = {zero, zero, zero}, c[3] = {zero, zero, zero}, m[3] = {zero, zero, zero};
   for_each_slot<6, 2>(v, e, lane, G, [&](int f, int32_t ent) {
     const int b = v.D - entry_level(ent);
     if (f < 3) {
-      const double w = face_weight(a, b);
-      const double t = w * (double(u[entry_idx(ent)]) - ul);
-      g0 += f == 0 ? t : 0.0;
-      g1 += f == 1 ? t : 0.0;
-      g2 += f == 2 ? t : 0.0;
-      c0 += f == 0 ? w : 0.0;
-      c1 += f == 1 ? w : 0.0;
-      c2 += f == 2 ? w : 0.0;
+      ff w;
+      const ff t = grad_term(a, b, u[entry_idx(ent)], ul, &w);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        g[d] = ff_add(g[d], f == d ? t : zero);
+        c[d] = ff_add(c[d], f == d ? w : zero);
+      }
     } else {
-      // (h_n^3 / h^3) alpha_nl / Delta
-      const double w = face_weight(b, a) * pow2d(3 * (b - a));
-      const double t = w * double(p[int64_t(f - 3) * v.stride + entry_idx(ent)]);
-      m0 += f == 3 ? t : 0.0;
-      m1 += f == 4 ? t : 0.0;
-      m2 += f == 5 ? t : 0.0;
+      const ff t = div_term(a, b, p[int64_t(f - 3) * v.stride + entry_idx(ent)]);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) m[d] = ff_add(m[d], f == 3 + d ? t : zero);
     }
   });
-  g0 = group_sum_d<G>(g0);
-  g1 = group_sum_d<G>(g1);
-  g2 = group_sum_d<G>(g2);
-  c0 = group_sum_d<G>(c0);
-  c1 = group_sum_d<G>(c1);
-  c2 = group_sum_d<G>(c2);
-  m0 = group_sum_d<G>(m0);
-  m1 = group_sum_d<G>(m1);
-  m2 = group_sum_d<G>(m2);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    g[d] = group_sum_ff<G>(g[d]);
+    c[d] = group_sum_ff<G>(c[d]);
+    m[d] = group_sum_ff<G>(m[d]);
+  }
   if (lane != 0 || !valid) return;
-  const double dv = (c0 * double(p[l]) - m0) + (c1 * double(p[v.stride + l]) - m1) +
-                    (c2 * double(p[2 * v.stride + l]) - m2);
-  leaf_terms(soff, samp, l, a, ul, g0 * g0 + g1 * g1 + g2 * g2, dv, lambda, gamma, sp, sd);
+  const float pl[3] = {p[l], p[v.stride + l], p[2 * v.stride + l]};
+  leaf_terms(soff, samp, l, a, ul, g, c, m, pl, lambda, gamma, sp, sd);
 }
 
 constexpr int kEnergyListLanes = 4;
@@ -505,23 +690,25 @@ constexpr int kEnergyListLanes = 4;
 // Launch layout: hb blocks of heavy leaves (a warp per leaf, strided over
 // the heavy set), lb blocks of list leaves (kEnergyListLanes lanes per leaf,
 // strided over the list set), then light leaves (a thread each, strided over
-// all leaves, skipping those with a finer-neighbour list).  Each block writes
-// its (primal, dual) partial; all sums are in a fixed order.
+// all leaves, skipping those with a finer-neighbour list).  Each thread sums
+// its leaves in float-float; each block writes its (primal, dual) partial in
+// float64; all sums are in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 4) k_energy(View v, const float* __restrict__ u,
                                                         const float* __restrict__ p,
                                                         const uint32_t* __restrict__ soff,
-                                                        const T* __restrict__ samp, double lambda,
-                                                        double gamma, Segments sg, int hb, int lb,
+                                                        const T* __restrict__ samp, double lambda_d,
+                                                        double gamma_d, Segments sg, int hb, int lb,
                                                         double* __restrict__ partial) {
   __shared__ double red[kThreads / 32];
-  double sp = 0.0, sd = 0.0;
+  const ff lambda = ff_of(lambda_d), gamma = ff_of(gamma_d);
+  ff sp{0.0f, 0.0f}, sd{0.0f, 0.0f};
   const int b = int(blockIdx.x);
   if (b < hb) {
     const int w = b * (kThreads / 32) + int(threadIdx.x >> 5), nw = hb * (kThreads / 32);
     for (int q = w; q < sg.n_heavy; q += nw)
-      leaf_energy<32>(v, u, p, soff, samp, lambda, gamma, sg.heavy[q], int(threadIdx.x & 31), true,
-                      &sp, &sd);
+      group_energy<32>(v, u, p, soff, samp, lambda, gamma, sg.heavy[q], int(threadIdx.x & 31), true,
+                       &sp, &sd);
   } else if (b < hb + lb) {
     constexpr int G = kEnergyListLanes;
     const int t = (b - hb) * kThreads + int(threadIdx.x);
@@ -530,23 +717,27 @@ __global__ void __launch_bounds__(kThreads, 4) k_energy(View v, const float* __r
     for (int r = 0; r < rounds; ++r) {
       const int q = gi + r * ng;
       const bool valid = q < sg.n_list;
-      leaf_energy<G>(v, u, p, soff, samp, lambda, gamma, sg.list[valid ? q : sg.n_list - 1], t % G,
-                     valid, &sp, &sd);
+      group_energy<G>(v, u, p, soff, samp, lambda, gamma, sg.list[valid ? q : sg.n_list - 1], t % G,
+                      valid, &sp, &sd);
     }
   } else {
     const int nb = int(gridDim.x) - hb - lb;
     for (int64_t l = int64_t(b - hb - lb) * blockDim.x + threadIdx.x; l < v.n;
          l += int64_t(nb) * blockDim.x) {
+      int32_t e[6];
       bool listed = false;
 #pragma unroll
-      for (int f = 0; f < 6; ++f) listed |= is_list(v.nbr[int64_t(f) * v.stride + l]);
+      for (int f = 0; f < 6; ++f) {
+        e[f] = v.nbr[int64_t(f) * v.stride + l];
+        listed |= is_list(e[f]);
+      }
       if (listed) continue;   // summed by a heavy or list group
-      leaf_energy<1>(v, u, p, soff, samp, lambda, gamma, l, 0, true, &sp, &sd);
+      light_energy(v, u, p, soff, samp, lambda, gamma, l, e, &sp, &sd);
     }
   }
   // block partial in a fixed order
-  const double bp = block_sum_d(sp, red);
-  const double bd = block_sum_d(sd, red);
+  const double bp = block_sum_d(ff_double(sp), red);
+  const double bd = block_sum_d(ff_double(sd), red);
   if (threadIdx.x == 0) {
     partial[2 * blockIdx.x] = bp;
     partial[2 * blockIdx.x + 1] = bd;
@@ -588,16 +779,16 @@ inline unsigned blocks_for(int64_t n, int threads) { return unsigned((n + thread
 
 }  // namespace
 
-inline unsigned grid_of(int64_t n, const Segments& sg, int list_lanes) {
-  return blocks_for(n, kThreads) + blocks_for(int64_t(sg.n_list) * list_lanes, kThreads) +
-         unsigned(heavy_blocks(sg));
+inline unsigned grid_of(int64_t n, const Segments& sg, int list_lanes, int light_leaves) {
+  return blocks_for(n, kThreads * light_leaves) +
+         blocks_for(int64_t(sg.n_list) * list_lanes, kThreads) + unsigned(heavy_blocks(sg));
 }
 
 cudaError_t launch_dual(View v, const float* ubar, float* p, const float* sigma, float lambda,
                         LeafSets ls, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
   const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
-  k_dual<false><<<grid_of(v.n, sg, kDualListLanes), kThreads, 0, s>>>(v, ubar, p, sigma, lambda, sg, 0.0f);
+  k_dual<false><<<grid_of(v.n, sg, kDualListLanes, kDualLightLeaves), kThreads, 0, s>>>(v, ubar, p, sigma, lambda, sg, 0.0f);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -606,7 +797,7 @@ cudaError_t launch_dual_init(View v, const float* u, float* p, float lambda, flo
                              cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
   const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
-  k_dual<true><<<grid_of(v.n, sg, kDualListLanes), kThreads, 0, s>>>(v, u, p, nullptr, lambda, sg, g0);
+  k_dual<true><<<grid_of(v.n, sg, kDualListLanes, kDualLightLeaves), kThreads, 0, s>>>(v, u, p, nullptr, lambda, sg, g0);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -616,7 +807,7 @@ cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const f
                           LeafSets ls, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
   const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
-  const unsigned nb = grid_of(v.n, sg, kPrimalListLanes);
+  const unsigned nb = grid_of(v.n, sg, kPrimalListLanes, kPrimalLightLeaves);
   if (fp16)
     k_primal<__half><<<nb, kThreads, 0, s>>>(v, u, ubar, p, tau, soff,
                                              reinterpret_cast<const __half*>(samp), gamma, sg);
@@ -659,7 +850,10 @@ cudaError_t launch_energy(View v, const float* u, const float* p, const uint32_t
                           const void* samp, bool fp16, double lambda, double gamma, LeafSets ls,
                           double* partial, double* out3, cudaStream_t s) {
   const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
-  const EnergyLayout g = energy_layout(v.n, sg, kThreads, kEnergyBlocks);
+  // light blocks: one wave of resident blocks (4 per SM), strided over the leaves
+  const int64_t wave = int64_t(sm_count()) * 4;
+  const int64_t per = std::max<int64_t>(kThreads, (v.n + wave - 1) / wave);
+  const EnergyLayout g = energy_layout(v.n, sg, per, kEnergyBlocks);
   if (fp16)
     energy_launch<__half>(g, v, u, p, soff, samp, lambda, gamma, sg, partial, s);
   else
