@@ -127,6 +127,8 @@ __global__ void __launch_bounds__(kThreads, kIterMinBlocks) k_dual(View v, const
   const int lb = (sg.n_list * kDualListLanes + kThreads - 1) / kThreads;
   const int b = int(blockIdx.x);
   if (b < hb + lb) {
+    grid_dep_wait();
+    grid_dep_launch();
     if (b < hb)
       dual_group<INIT, kHeavyLanes>(v, ubar, p, sigma, lambda, g0, sg.heavy, sg.n_heavy, b);
     else
@@ -153,17 +155,23 @@ __global__ void __launch_bounds__(kThreads, kIterMinBlocks) k_dual(View v, const
 #pragma unroll
     for (int d = 0; d < 3; ++d) e[j][d] = v.nbr[d * st + lc];
     lev[j] = v.level[lc];
+    sl[j] = INIT ? 0.0f : sigma[lc];
+  }
+  // the structure arrays above are read before the previous kernel ends;
+  // ubar and p only after it
+  grid_dep_wait();
+  grid_dep_launch();
+  float x[K][3];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const int64_t lc = l[j] < v.n ? l[j] : v.n - 1;
     ul[j] = ubar[lc];
 #pragma unroll
     for (int d = 0; d < 3; ++d) q[j][d] = p[d * st + lc];
-    sl[j] = INIT ? 0.0f : sigma[lc];
-    if (l[j] >= v.n) l[j] = -1;
-  }
-  float x[K][3];
-#pragma unroll
-  for (int j = 0; j < K; ++j)
 #pragma unroll
     for (int d = 0; d < 3; ++d) x[j][d] = ubar[e[j][d] >= 0 ? entry_idx(e[j][d]) : 0u];
+    if (l[j] >= v.n) l[j] = -1;
+  }
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     const float h = edge_f(v.D, lev[j]);
@@ -301,18 +309,24 @@ __device__ __forceinline__ void primal_light(const View& v, float* __restrict__ 
 #pragma unroll
     for (int f = 0; f < 6; ++f) e[j][f] = v.nbr[f * st + lc];
     lev[j] = v.level[lc];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) q[j][d] = p[d * st + lc];
     tl[j] = tau[lc];
-    ul[j] = u[lc];
     o[j] = soff[lc];
     W[j] = int(soff[lc + 1] - o[j]);
   }
+  // the structure arrays above are read before the previous kernel ends;
+  // u and p only after it
+  grid_dep_wait();
+  grid_dep_launch();
   float pn[K][3];
 #pragma unroll
-  for (int j = 0; j < K; ++j)
+  for (int j = 0; j < K; ++j) {
+    const int64_t lc = l[j] < v.n ? l[j] : v.n - 1;
+    ul[j] = u[lc];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) q[j][d] = p[d * st + lc];
 #pragma unroll
     for (int d = 0; d < 3; ++d) pn[j][d] = p[d * st + (e[j][3 + d] >= 0 ? entry_idx(e[j][3 + d]) : 0u)];
+  }
   // prox argument x, scaled weight t and the bisection state [lo, hi) per leaf
   float x[K], t[K], flo[K], fhi[K];
   int lo[K], hi[K];
@@ -390,6 +404,8 @@ __global__ void __launch_bounds__(kThreads, kIterMinBlocks) k_primal(View v, flo
   const int lb = (sg.n_list * kPrimalListLanes + kThreads - 1) / kThreads;
   const int b = int(blockIdx.x);
   if (b < hb + lb) {
+    grid_dep_wait();
+    grid_dep_launch();
     if (b < hb)
       primal_group<kHeavyLanes>(v, u, ubar, p, tau, soff, samp, gamma, sg.heavy, sg.n_heavy, b);
     else
@@ -462,34 +478,35 @@ __device__ __forceinline__ ff ff_mul(ff x, ff y) {
   return ff_fast_sum(p.hi, __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo)));
 }
 
-// sqrt(x) for x >= 0: s = sqrt(hi) rounded, then one Newton correction
-// (x - s^2) / (2 s), where hi - s^2 is exact (the two are within a factor 2).
+// sqrt(x) for x >= 0: s within a few ulps of sqrt(hi) (hi rsqrt(hi); the
+// correctly rounded root below 2^-100, where the approximation loses
+// precision), then one Newton correction (x - s^2) / (2 s), where hi - s^2
+// is exact (the two are within a factor 2).
 __device__ __forceinline__ ff ff_sqrt(ff x) {
   if (!(x.hi > 0.0f)) return {0.0f, 0.0f};
-  const float s = __fsqrt_rn(x.hi);
+  const float s = x.hi >= 0x1p-100f ? x.hi * rsqrtf(x.hi) : __fsqrt_rn(x.hi);
   const ff sq = ff_two_prod(s, s);
   const float r = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, sq.hi), sq.lo), x.lo);
   return ff_fast_sum(s, __fdividef(r, 2.0f * s));
 }
 
-// 1 / x for x > 0: r = 1 / hi rounded, then r + r (1 - x r), where 1 - x r
-// is formed from the exact product.
+// 1 / x for x > 0: r within a few ulps of 1 / hi, then r + r (1 - x r),
+// where 1 - x r is formed from the exact product.
 __device__ __forceinline__ ff ff_recip(ff x) {
-  const float r = __frcp_rn(x.hi);
+  const float r = __fdividef(1.0f, x.hi);
   const ff xr = ff_mul_f(x, r);
   const float e = __fsub_rn(__fsub_rn(1.0f, xr.hi), xr.lo);
   return ff_fast_sum(r, __fmul_rn(r, e));
 }
 
-__device__ __forceinline__ ff ff_of(double d) {
-  const float hi = __double2float_rn(d);
-  return {hi, __double2float_rn(d - double(hi))};
+// d as a pair (host side: kernel arguments)
+inline ff ff_split(double d) {
+  const float hi = float(d);
+  return {hi, float(d - double(hi))};
 }
 
 __device__ __forceinline__ double ff_double(ff x) { return double(x.hi) + double(x.lo); }
 
-// 2^e as a float, -126 <= e <= 127
-__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
 
 // 1 / (1 + 2^d), d = 0..15, split into a float pair: 1 / Delta for leaves of
 // edges 2^a and 2^b is 2^(1 - min(a, b)) / (1 + 2^|a - b|).
@@ -511,6 +528,13 @@ __device__ __forceinline__ ff face_weight(int a, int b, int extra) {
   const int d = a < b ? b - a : a - b;
   const float s = pow2f(1 - lo + (b < a ? 2 * (b - a) : 0) + extra);
   return {kInvHi[d] * s, kInvLo[d] * s};
+}
+
+// alpha / Delta 2^extra for a single face neighbour, which is never finer
+// (b >= a, alpha = 1): the table pair times 2^(1 - a + extra).
+__device__ __forceinline__ ff single_weight(int a, int b, int extra) {
+  const float s = pow2f(1 - a + extra);
+  return {kInvHi[b - a] * s, kInvLo[b - a] * s};
 }
 
 // +face term of neighbour value um: alpha / Delta (um - ul), and the weight
@@ -589,17 +613,6 @@ __device__ __forceinline__ void leaf_terms(const uint32_t* __restrict__ soff,
   *sd = ff_add(*sd, ff_scale(ff_add(ff_mul(rc, dd), ff_neg(ff_mul_f(dv, xs))), vol));
 }
 
-__device__ __forceinline__ double block_sum_d(double x, double* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
-  __syncthreads();
-  double t = 0.0;
-  for (int w = 0; w < kThreads / 32; ++w) t += red[w];
-  return t;
-}
-
 // Sum over the G lanes of a group of one pair (groups aligned in the warp;
 // every lane of the warp takes part; lane 0's sum is in a fixed order).
 template <int G>
@@ -608,6 +621,19 @@ __device__ __forceinline__ ff group_sum_ff(ff x) {
   for (int o = G / 2; o > 0; o >>= 1)
     x = ff_add(x, ff{__shfl_xor_sync(kFull, x.hi, o), __shfl_xor_sync(kFull, x.lo, o)});
   return x;
+}
+
+// Block sum of one pair per thread: each warp's sum in float-float, then the
+// warps' sums in float64 in a fixed order (the result is thread 0's).
+__device__ __forceinline__ double block_sum_ff(ff x, double* red) {
+  x = group_sum_ff<32>(x);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ff_double(x);
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+  return t;
 }
 
 // Energy terms of a light leaf l (single entries on every face): the six
@@ -632,12 +658,14 @@ __device__ __forceinline__ void light_energy(const View& v, const float* __restr
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const ff zero{0.0f, 0.0f};
-    ff w;
-    const ff t = grad_term(a, e[d] >= 0 ? v.D - entry_level(e[d]) : a, x[d], ul, &w);
-    g[d] = e[d] >= 0 ? t : zero;
+    const int bp = e[d] >= 0 ? v.D - entry_level(e[d]) : a;
+    const ff w = single_weight(a, bp, 0);
+    g[d] = e[d] >= 0 ? ff_mul(w, ff_two_sum(x[d], -ul)) : zero;
     c[d] = e[d] >= 0 ? w : zero;
-    const ff s = div_term(a, e[3 + d] >= 0 ? v.D - entry_level(e[3 + d]) : a, x[3 + d]);
-    m[d] = e[3 + d] >= 0 ? s : zero;
+    // (h_n^3 / h^3) alpha_nl / Delta = (h_n / h) / Delta for a neighbour n
+    // of the same size or coarser
+    const int bn = e[3 + d] >= 0 ? v.D - entry_level(e[3 + d]) : a;
+    m[d] = e[3 + d] >= 0 ? ff_mul_f(single_weight(a, bn, bn - a), x[3 + d]) : zero;
   }
   leaf_terms(soff, samp, l, a, ul, g, c, m, pl, lambda, gamma, sp, sd);
 }
@@ -658,22 +686,28 @@ __device__ __forceinline__ void group_energy(const View& v, const float* __restr
   const float ul = u[l];
   const ff zero{0.0f, 0.0f};
   ff g[3] = {zero, zero, zero}, c[3] = {zero, zero, zero}, m[3] = {zero, zero, zero};
-  for_each_slot<6, 2>(v, e, lane, G, [&](int f, int32_t ent) {
-    const int b = v.D - entry_level(ent);
-    if (f < 3) {
-      ff w;
-      const ff t = grad_term(a, b, u[entry_idx(ent)], ul, &w);
+  // face by face (unrolled, so each sum is a register): this lane takes the
+  // entries lane, lane + G, ... of the face's list, or the single entry on lane 0
+  int cnt[6];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        g[d] = ff_add(g[d], f == d ? t : zero);
-        c[d] = ff_add(c[d], f == d ? w : zero);
+  for (int f = 0; f < 6; ++f)
+    cnt[f] = e[f] >= 0 ? 1 : (e[f] == kEmpty ? 0 : v.ovf[list_start(e[f])]);
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const int32_t* lst = e[f] >= 0 ? nullptr : v.ovf + list_start(e[f]) + 1;
+    for (int k = lane; k < cnt[f]; k += G) {
+      const int32_t ent = e[f] >= 0 ? e[f] : lst[k];
+      const int b = v.D - entry_level(ent);
+      if (f < 3) {
+        ff w;
+        const ff t = grad_term(a, b, u[entry_idx(ent)], ul, &w);
+        g[f] = ff_add(g[f], t);
+        c[f] = ff_add(c[f], w);
+      } else {
+        m[f - 3] = ff_add(m[f - 3], div_term(a, b, p[int64_t(f - 3) * v.stride + entry_idx(ent)]));
       }
-    } else {
-      const ff t = div_term(a, b, p[int64_t(f - 3) * v.stride + entry_idx(ent)]);
-#pragma unroll
-      for (int d = 0; d < 3; ++d) m[d] = ff_add(m[d], f == 3 + d ? t : zero);
     }
-  });
+  }
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     g[d] = group_sum_ff<G>(g[d]);
@@ -697,11 +731,10 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, 4) k_energy(View v, const float* __restrict__ u,
                                                         const float* __restrict__ p,
                                                         const uint32_t* __restrict__ soff,
-                                                        const T* __restrict__ samp, double lambda_d,
-                                                        double gamma_d, Segments sg, int hb, int lb,
+                                                        const T* __restrict__ samp, ff lambda,
+                                                        ff gamma, Segments sg, int hb, int lb,
                                                         double* __restrict__ partial) {
   __shared__ double red[kThreads / 32];
-  const ff lambda = ff_of(lambda_d), gamma = ff_of(gamma_d);
   ff sp{0.0f, 0.0f}, sd{0.0f, 0.0f};
   const int b = int(blockIdx.x);
   if (b < hb) {
@@ -736,8 +769,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_energy(View v, const float* __r
     }
   }
   // block partial in a fixed order
-  const double bp = block_sum_d(ff_double(sp), red);
-  const double bd = block_sum_d(ff_double(sd), red);
+  const double bp = block_sum_ff(sp, red);
+  const double bd = block_sum_ff(sd, red);
   if (threadIdx.x == 0) {
     partial[2 * blockIdx.x] = bp;
     partial[2 * blockIdx.x + 1] = bd;
@@ -779,6 +812,30 @@ inline unsigned blocks_for(int64_t n, int threads) { return unsigned((n + thread
 
 }  // namespace
 
+// The iteration kernels are launched with programmatic dependent launch
+// (see grid_dep_wait): a kernel's launch, block start-up and structure reads
+// overlap the tail of the kernel before it.
+constexpr bool kIterPDL = true;
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_iter(void (*kernel)(KArgs...), unsigned grid, cudaStream_t s, Args... args) {
+  if (!kIterPDL) {
+    kernel<<<grid, kThreads, 0, s>>>(args...);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 inline unsigned grid_of(int64_t n, const Segments& sg, int list_lanes, int light_leaves) {
   return blocks_for(n, kThreads * light_leaves) +
          blocks_for(int64_t(sg.n_list) * list_lanes, kThreads) + unsigned(heavy_blocks(sg));
@@ -788,9 +845,10 @@ cudaError_t launch_dual(View v, const float* ubar, float* p, const float* sigma,
                         LeafSets ls, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
   const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
-  k_dual<false><<<grid_of(v.n, sg, kDualListLanes, kDualLightLeaves), kThreads, 0, s>>>(v, ubar, p, sigma, lambda, sg, 0.0f);
+  const cudaError_t e = launch_iter(k_dual<false>, grid_of(v.n, sg, kDualListLanes, kDualLightLeaves),
+                                    s, v, ubar, p, sigma, lambda, sg, 0.0f);
   count_launches(1);
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_dual_init(View v, const float* u, float* p, float lambda, float g0, LeafSets ls,
@@ -808,14 +866,13 @@ cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const f
   if (v.n <= 0) return cudaSuccess;
   const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
   const unsigned nb = grid_of(v.n, sg, kPrimalListLanes, kPrimalLightLeaves);
-  if (fp16)
-    k_primal<__half><<<nb, kThreads, 0, s>>>(v, u, ubar, p, tau, soff,
-                                             reinterpret_cast<const __half*>(samp), gamma, sg);
-  else
-    k_primal<float><<<nb, kThreads, 0, s>>>(v, u, ubar, p, tau, soff,
-                                            reinterpret_cast<const float*>(samp), gamma, sg);
+  const cudaError_t e =
+      fp16 ? launch_iter(k_primal<__half>, nb, s, v, u, ubar, p, tau, soff,
+                         reinterpret_cast<const __half*>(samp), gamma, sg)
+           : launch_iter(k_primal<float>, nb, s, v, u, ubar, p, tau, soff,
+                         reinterpret_cast<const float*>(samp), gamma, sg);
   count_launches(1);
-  return cudaGetLastError();
+  return e;
 }
 
 size_t energy_tmp_bytes(int64_t) { return size_t(2 * kEnergyBlocks) * sizeof(double); }
@@ -842,8 +899,8 @@ template <typename T>
 void energy_launch(EnergyLayout g, View v, const float* u, const float* p, const uint32_t* soff,
                    const void* samp, double lambda, double gamma, Segments sg, double* partial,
                    cudaStream_t s) {
-  k_energy<T><<<g.nb, kThreads, 0, s>>>(v, u, p, soff, reinterpret_cast<const T*>(samp), lambda,
-                                        gamma, sg, g.hb, g.lb, partial);
+  k_energy<T><<<g.nb, kThreads, 0, s>>>(v, u, p, soff, reinterpret_cast<const T*>(samp),
+                                        ff_split(lambda), ff_split(gamma), sg, g.hb, g.lb, partial);
 }
 
 cudaError_t launch_energy(View v, const float* u, const float* p, const uint32_t* soff,

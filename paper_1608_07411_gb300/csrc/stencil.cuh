@@ -18,7 +18,23 @@ constexpr int kThreads = 256;
 // registers) measured fastest over 4..8 on both the 256^3 and 512^3 workloads.
 constexpr int kIterMinBlocks = 6;
 
-__device__ __forceinline__ float edge_f(int D, int level) { return float(1u << (D - level)); }
+// Programmatic dependent launch (a launch attribute on sm_90 and later): a
+// kernel launched with it may start while the kernel before it in the stream
+// is still running.  Before grid_dep_wait() it may read only data that no
+// kernel of the last few launches writes (the octree's structure arrays);
+// after it, everything the previous kernels wrote is visible.  Every block
+// calls grid_dep_launch() only after its own wait, which lets the next kernel
+// start: the next kernel's early reads then never overlap a kernel that is
+// still waiting.  Without the attribute both are no-ops.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// 2^e as a float, -126 <= e <= 127 (built from the exponent field)
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+__device__ __forceinline__ float edge_f(int D, int level) { return pow2f(D - level); }
 
 // 1 / Delta for leaves of edges h and hm: 2 / (h + hm), exact sum of powers of two.
 __device__ __forceinline__ float inv_delta(float h, float hm) { return __fdividef(2.0f, h + hm); }
