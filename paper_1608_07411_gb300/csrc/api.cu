@@ -31,7 +31,7 @@ thread_local std::string g_create_error;
 enum Buf {
   B_SCAN, B_U0, B_PYR, B_FLAGS, B_POS, B_CNT, B_OVFC, B_CLS, B_OUTC, B_JL, B_SRC, B_LIST,
   B_SMALL, B_PART, B_BIG, B_LONGQ, B_FWD, B_AUX, B_FULL, B_PENDQ, B_Q, B_QF, B_QD, B_QT, B_LFL,
-  B_MG, B_MC, B_MN, B_MV, B_MT, B_FTC, B_FTT, B_FTL, B_FTH, B_NUM
+  B_MG, B_MC, B_MN, B_MV, B_MT, B_FTC, B_FTT, B_FTL, B_FTH, B_RPYR, B_NUM
 };
 
 struct Bufs {
@@ -622,9 +622,15 @@ ofu_status ofu_integrate_frames(ofu_ctx* ctx, int32_t F, int32_t H, int32_t W, c
   ST(ensure(ctx, B_SCAN, scan_tmp_items<uint32_t>(nvox) * 2, &tmp));
   uint64_t* small;
   ST(ensure(ctx, B_SMALL, 16, &small));
+  // min / max pyramid of the range maps for the scan's frame classification
+  RangePyr rp = range_pyr_dims(H, W);
+  float2* rtex = nullptr;
+  ST(ensure(ctx, B_RPYR, size_t(std::max<int64_t>(int64_t(F) * rp.frame_texels, 1)), &rtex));
+  rp.tex = rtex;
+  CU(launch_range_pyr(ctx->depth, F, H, W, rp, rtex, ctx->stream));
   // pos is free until the leaf flags are scanned: it holds the voxels whose
   // median needs a sort
-  CU(launch_dense_u0(ctx->depth, ctx->cams, F, H, W, g, u0, pos,
+  CU(launch_dense_u0(ctx->depth, ctx->cams, F, H, W, g, rp, u0, pos,
                      reinterpret_cast<unsigned long long*>(small + 12), ctx->stream));
   CU(launch_pyramid(u0, D, pyr, pyr + npyr, ctx->stream));
   CU(launch_leaf_flags(pyr, pyr + npyr, D, ctx->prm.spread_tau, flags, ctx->stream));

@@ -229,44 +229,166 @@ __device__ __forceinline__ int warp_samples(const Cam* sc, const float* depth, i
       F, a, mn, mx);
 }
 
-// Median field, first pass: a thread per finest voxel walks all frames and
+// ---------------------------------------------------------------------------
+// Frame classification of a box of voxel centres.  A warp of the median scan
+// holds 32 Morton-consecutive finest voxels, a 4 x 4 x 2 box of centres.  For
+// most frames the whole box either sees one value or is unobserved: it lies
+// in front of the surface by more than delta (every Eq. 1 sample is +1), or
+// behind it by more than eta, outside the image or behind the camera (no
+// sample).  The test bounds the box's projection by its 8 corners (the
+// projection of a convex box in front of the camera is the hull of the
+// corners'), the ranges under it by the range pyramid, and the distances by
+// the nearest point and the farthest corner.  Every bound is widened by a
+// margin far above float32 rounding (relative 1e-5 against errors near 1e-6),
+// so a frame classified this way gives every voxel exactly what Eq. 1 in
+// float32 gives it; any other frame is "mixed" and evaluated per voxel.
+constexpr int kObsMixed = 0, kObsOne = 1, kObsNone = 2;
+
+// Min and max of the valid ranges over the pixel rectangle [px0, px1] x
+// [py0, py1] (inside the image) of frame f, from the smallest pyramid level
+// at which the rectangle touches at most 2 x 2 texels (a superset of it).
+__device__ __forceinline__ float2 range_bounds(const RangePyr& rp, const int* lv, const float* range,
+                                               int f, int H, int W, int px0, int px1, int py0,
+                                               int py1) {
+  int k = 0;
+  while (k < rp.nl && ((px1 >> k) - (px0 >> k) > 1 || (py1 >> k) - (py0 >> k) > 1)) ++k;
+  float lo = CUDART_INF_F, hi = -CUDART_INF_F;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int x = (a ? px1 : px0) >> k, y = (b ? py1 : py0) >> k;
+      float2 t;
+      if (k == 0) {
+        const float r = range[size_t(f) * H * W + size_t(y) * W + x];
+        t.x = t.y = r > 0.0f ? r : -CUDART_INF_F;
+      } else {
+        const int wk = lv[k], hk = lv[kMaxRangeLevels + 1 + k], ok = lv[2 * (kMaxRangeLevels + 1) + k];
+        t = rp.tex[f * rp.frame_texels + ok + int64_t(min(y, hk - 1)) * wk + min(x, wk - 1)];
+      }
+      lo = fminf(lo, t.x);
+      hi = fmaxf(hi, t.y);
+    }
+  return make_float2(lo, hi);
+}
+
+// Class of frame f for every voxel centre in the box with centre (bx, by, bz)
+// and half extents (hx, hy, hz); lv holds the pyramid's level widths,
+// heights and offsets.
+__device__ __forceinline__ int classify_box(const Cam& k, const float* range, const RangePyr& rp,
+                                            const int* lv, int f, int H, int W, float bx, float by,
+                                            float bz, float hx, float hy, float hz, float delta,
+                                            float eta) {
+  const float dx = bx - k.c[0], dy = by - k.c[1], dz = bz - k.c[2];
+  const float xc = k.r[0] * dx + k.r[3] * dy + k.r[6] * dz;
+  const float yc = k.r[1] * dx + k.r[4] * dy + k.r[7] * dz;
+  const float zc = k.r[2] * dx + k.r[5] * dy + k.r[8] * dz;
+  const float mz = 1e-5f * (fabsf(dx) + fabsf(dy) + fabsf(dz) + hx + hy + hz);
+  const float ez = fabsf(k.r[2]) * hx + fabsf(k.r[5]) * hy + fabsf(k.r[8]) * hz;
+  if (zc + ez < -mz) return kObsNone;   // the whole box behind the camera
+  if (!(zc - ez > mz)) return kObsMixed;
+  float u0 = CUDART_INF_F, u1 = -CUDART_INF_F, v0 = CUDART_INF_F, v1 = -CUDART_INF_F;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float sx = c & 1 ? hx : -hx, sy = c & 2 ? hy : -hy, sz = c & 4 ? hz : -hz;
+    const float X = xc + k.r[0] * sx + k.r[3] * sy + k.r[6] * sz;
+    const float Y = yc + k.r[1] * sx + k.r[4] * sy + k.r[7] * sz;
+    const float iz = __frcp_rn(zc + k.r[2] * sx + k.r[5] * sy + k.r[8] * sz);
+    const float u = k.fx * (X * iz) + k.cx, v = k.fy * (Y * iz) + k.cy;
+    u0 = fminf(u0, u);
+    u1 = fmaxf(u1, u);
+    v0 = fminf(v0, v);
+    v1 = fmaxf(v1, v);
+  }
+  const float mu = 1e-4f * (fmaxf(fabsf(u0), fabsf(u1)) + fabsf(k.cx)) + 1e-3f;
+  const float mv = 1e-4f * (fmaxf(fabsf(v0), fabsf(v1)) + fabsf(k.cy)) + 1e-3f;
+  const float ua = u0 - mu, ub = u1 + mu, va = v0 - mv, vb = v1 + mv;
+  if (ub < 0.0f || ua >= float(W) || vb < 0.0f || va >= float(H)) return kObsNone;
+  if (!(ua >= 0.0f && ub < float(W) && va >= 0.0f && vb < float(H))) return kObsMixed;
+  const float2 r = range_bounds(rp, lv, range, f, H, W, int(floorf(ua)), int(floorf(ub)),
+                                int(floorf(va)), int(floorf(vb)));
+  const float nx = fmaxf(fabsf(dx) - hx, 0.0f), ny = fmaxf(fabsf(dy) - hy, 0.0f),
+              nz = fmaxf(fabsf(dz) - hz, 0.0f);
+  const float fx = fabsf(dx) + hx, fy = fabsf(dy) + hy, fz = fabsf(dz) + hz;
+  const float dmin = sqrtf(nx * nx + ny * ny + nz * nz), dmax = sqrtf(fx * fx + fy * fy + fz * fz);
+  const float md = 1e-5f * dmax;
+  // every pixel valid and every phi >= delta: all samples +1
+  if (r.x > 0.0f && r.x - (dmax + md) >= delta + 1e-5f * (r.x + dmax)) return kObsOne;
+  // every pixel invalid or every phi < -eta: unobserved (r.y = -inf: all invalid)
+  if (r.y - (dmin - md) < -eta - 1e-5f * (fabsf(r.y) + dmax)) return kObsNone;
+  return kObsMixed;
+}
+
+// Median field, first pass: a thread per finest voxel walks the frames and
 // keeps W, min and max of the observed Eq. 1 samples.  The median is final
 // where W = 0 (-1) or every observed sample is the same value; the other
 // voxels (near a surface) are queued for the warp sort of k_dense_u0.
-// Warps stride over the voxels together, so every lane reaches the ballot.
+// Warps stride over the voxels together, so every lane reaches the ballots.
+// A full warp first classifies the frames against its box of centres (lane
+// i the frames i, i + 32, ...); only the mixed frames are evaluated per voxel.
 __global__ void __launch_bounds__(256) k_dense_scan(const float* __restrict__ depth,
                                                     const Cam* __restrict__ cams, int F, int H,
-                                                    int W, Geo g, int64_t nvox,
+                                                    int W, Geo g, RangePyr rp, int64_t nvox,
                                                     double* __restrict__ u0,
                                                     uint32_t* __restrict__ queue,
                                                     unsigned long long* __restrict__ nqueue) {
   extern __shared__ float4 smem_dyn[];
+  __shared__ int lv[3 * (kMaxRangeLevels + 1)];
   Cam* sc = reinterpret_cast<Cam*>(smem_dyn);
+  for (int i = threadIdx.x; i <= kMaxRangeLevels; i += blockDim.x) {
+    lv[i] = rp.w[i];
+    lv[kMaxRangeLevels + 1 + i] = rp.h[i];
+    lv[2 * (kMaxRangeLevels + 1) + i] = rp.off[i];
+  }
   stage_cams(sc, cams, F);
   const int lane = lane_id();
   for (int64_t m0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) & ~int64_t(31); m0 < nvox;
        m0 += int64_t(gridDim.x) * blockDim.x) {
     const int64_t m = m0 + lane;
-    bool sort = false;
-    if (m < nvox) {
-      const uint32_t ix = compact3(uint64_t(m)), iy = compact3(uint64_t(m) >> 1),
-                     iz = compact3(uint64_t(m) >> 2);
-      const float x = centre_coord(g.org[0], ix, 1, g.vox);
-      const float y = centre_coord(g.org[1], iy, 1, g.vox);
-      const float z = centre_coord(g.org[2], iz, 1, g.vox);
-      int cnt = 0;
-      float lo = CUDART_INF_F, hi = -CUDART_INF_F;
-      for (int i = 0; i < F; ++i) {
-        float t;
-        if (eq1_sample(sc[i], depth + size_t(i) * H * W, H, W, x, y, z, g.delta, g.eta, &t)) {
-          ++cnt;
-          lo = fminf(lo, t);
-          hi = fmaxf(hi, t);
-        }
+    const uint32_t ix = compact3(uint64_t(m)), iy = compact3(uint64_t(m) >> 1),
+                   iz = compact3(uint64_t(m) >> 2);
+    const float x = centre_coord(g.org[0], ix, 1, g.vox);
+    const float y = centre_coord(g.org[1], iy, 1, g.vox);
+    const float z = centre_coord(g.org[2], iz, 1, g.vox);
+    int cnt = 0;
+    float lo = CUDART_INF_F, hi = -CUDART_INF_F;
+    auto eval = [&](int i) {
+      float t;
+      if (eq1_sample(sc[i], depth + size_t(i) * H * W, H, W, x, y, z, g.delta, g.eta, &t)) {
+        ++cnt;
+        lo = fminf(lo, t);
+        hi = fmaxf(hi, t);
       }
-      sort = cnt > 0 && lo != hi;
-      if (!sort) u0[m] = cnt == 0 ? -1.0 : double(lo);
+    };
+    if (m0 + 32 <= nvox) {
+      // the warp's box: x over 4 voxels, y over 4, z over 2 (Morton bits
+      // x0 y0 z0 x1 y1 below the warp's base)
+      const uint32_t bx0 = compact3(uint64_t(m0)), by0 = compact3(uint64_t(m0) >> 1),
+                     bz0 = compact3(uint64_t(m0) >> 2);
+      const float xa = centre_coord(g.org[0], bx0, 1, g.vox), xb = centre_coord(g.org[0], bx0 + 3, 1, g.vox);
+      const float ya = centre_coord(g.org[1], by0, 1, g.vox), yb = centre_coord(g.org[1], by0 + 3, 1, g.vox);
+      const float za = centre_coord(g.org[2], bz0, 1, g.vox), zb = centre_coord(g.org[2], bz0 + 1, 1, g.vox);
+      int ones = 0;
+      for (int c0 = 0; c0 < F; c0 += 32) {
+        const int f = c0 + lane;
+        const int cls = f < F ? classify_box(sc[f], depth, rp, lv, f, H, W, 0.5f * (xa + xb),
+                                             0.5f * (ya + yb), 0.5f * (za + zb), 0.5f * (xb - xa),
+                                             0.5f * (yb - ya), 0.5f * (zb - za), g.delta, g.eta)
+                              : kObsNone;
+        ones += __popc(__ballot_sync(kFull, cls == kObsOne));
+        for (unsigned mixed = __ballot_sync(kFull, cls == kObsMixed); mixed; mixed &= mixed - 1)
+          eval(c0 + __ffs(mixed) - 1);
+      }
+      if (ones) {
+        cnt += ones;
+        lo = fminf(lo, 1.0f);
+        hi = fmaxf(hi, 1.0f);
+      }
+    } else if (m < nvox) {
+      for (int i = 0; i < F; ++i) eval(i);
     }
+    const bool sort = m < nvox && cnt > 0 && lo != hi;
+    if (m < nvox && !sort) u0[m] = cnt == 0 ? -1.0 : double(lo);
     const unsigned bal = __ballot_sync(kFull, sort);
     if (bal) {
       unsigned long long base = 0;
@@ -275,6 +397,44 @@ __global__ void __launch_bounds__(256) k_dense_scan(const float* __restrict__ de
       if (sort) queue[base + __popc(bal & ((1u << lane) - 1))] = uint32_t(m);
     }
   }
+}
+
+// Pyramid level 1 from the range maps, then each level from the one below.
+__global__ void k_rpyr_base(const float* __restrict__ range, int F, int H, int W, RangePyr rp,
+                            float2* __restrict__ tex) {
+  const int w1 = rp.w[1], h1 = rp.h[1];
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= int64_t(F) * w1 * h1) return;
+  const int f = int(i / (int64_t(w1) * h1));
+  const int r = int(i - int64_t(f) * w1 * h1);
+  const int ty = r / w1, tx = r - ty * w1;
+  float lo = CUDART_INF_F, hi = -CUDART_INF_F;
+  for (int y = 2 * ty; y < min(2 * ty + 2, H); ++y)
+    for (int x = 2 * tx; x < min(2 * tx + 2, W); ++x) {
+      const float v = range[size_t(f) * H * W + size_t(y) * W + x];
+      const float c = v > 0.0f ? v : -CUDART_INF_F;
+      lo = fminf(lo, c);
+      hi = fmaxf(hi, c);
+    }
+  tex[f * rp.frame_texels + rp.off[1] + r] = make_float2(lo, hi);
+}
+
+__global__ void k_rpyr_up(int F, int k, RangePyr rp, float2* __restrict__ tex) {
+  const int wk = rp.w[k], hk = rp.h[k], wb = rp.w[k - 1], hb = rp.h[k - 1];
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= int64_t(F) * wk * hk) return;
+  const int f = int(i / (int64_t(wk) * hk));
+  const int r = int(i - int64_t(f) * wk * hk);
+  const int ty = r / wk, tx = r - ty * wk;
+  const float2* below = tex + f * rp.frame_texels + rp.off[k - 1];
+  float lo = CUDART_INF_F, hi = -CUDART_INF_F;
+  for (int y = 2 * ty; y < min(2 * ty + 2, hb); ++y)
+    for (int x = 2 * tx; x < min(2 * tx + 2, wb); ++x) {
+      const float2 t = below[y * wb + x];
+      lo = fminf(lo, t.x);
+      hi = fmaxf(hi, t.y);
+    }
+  tex[f * rp.frame_texels + rp.off[k] + r] = make_float2(lo, hi);
 }
 
 // Median field, second pass: a warp per queued voxel (one frame per lane)
@@ -1434,16 +1594,16 @@ template cudaError_t scan_exclusive<double>(const double*, double*, int64_t, dou
 
 template <int P>
 static cudaError_t dense_u0_p(const float* depth, const Cam* cams, int F, int H, int W, Geo g,
-                              double* u0, uint32_t* queue, unsigned long long* nqueue,
-                              cudaStream_t s) {
+                              RangePyr rp, double* u0, uint32_t* queue,
+                              unsigned long long* nqueue, cudaStream_t s) {
   const int64_t nvox = int64_t(1) << (3 * g.D);
   cudaError_t e = cudaMemsetAsync(nqueue, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   const size_t sm0 = size_t(F) * sizeof(Cam);
   if (sm0 > 48 * 1024) cudaFuncSetAttribute(k_dense_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm0));
   const int64_t want = (nvox + 255) / 256, cap = int64_t(sm_count()) * 16;
-  k_dense_scan<<<unsigned(want < cap ? want : cap), 256, sm0, s>>>(depth, cams, F, H, W, g, nvox, u0,
-                                                                 queue, nqueue);
+  k_dense_scan<<<unsigned(want < cap ? want : cap), 256, sm0, s>>>(depth, cams, F, H, W, g, rp, nvox,
+                                                                 u0, queue, nqueue);
   count_launches(1);
   const size_t sm = sm0 + size_t(kWarpsPerBlock) * P * sizeof(float);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_dense_u0<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
@@ -1454,16 +1614,47 @@ static cudaError_t dense_u0_p(const float* depth, const Cam* cams, int F, int H,
 }
 
 cudaError_t launch_dense_u0(const float* depth, const Cam* cams, int F, int H, int W, Geo g,
-                            double* u0, uint32_t* queue, unsigned long long* nqueue,
+                            RangePyr rp, double* u0, uint32_t* queue, unsigned long long* nqueue,
                             cudaStream_t s) {
   switch (pad_frames(F)) {
-    case 32: return dense_u0_p<32>(depth, cams, F, H, W, g, u0, queue, nqueue, s);
-    case 64: return dense_u0_p<64>(depth, cams, F, H, W, g, u0, queue, nqueue, s);
-    case 128: return dense_u0_p<128>(depth, cams, F, H, W, g, u0, queue, nqueue, s);
-    case 256: return dense_u0_p<256>(depth, cams, F, H, W, g, u0, queue, nqueue, s);
-    case 512: return dense_u0_p<512>(depth, cams, F, H, W, g, u0, queue, nqueue, s);
+    case 32: return dense_u0_p<32>(depth, cams, F, H, W, g, rp, u0, queue, nqueue, s);
+    case 64: return dense_u0_p<64>(depth, cams, F, H, W, g, rp, u0, queue, nqueue, s);
+    case 128: return dense_u0_p<128>(depth, cams, F, H, W, g, rp, u0, queue, nqueue, s);
+    case 256: return dense_u0_p<256>(depth, cams, F, H, W, g, rp, u0, queue, nqueue, s);
+    case 512: return dense_u0_p<512>(depth, cams, F, H, W, g, rp, u0, queue, nqueue, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+RangePyr range_pyr_dims(int H, int W) {
+  RangePyr rp{};
+  int w = W, h = H, off = 0, k = 0;
+  rp.w[0] = W;
+  rp.h[0] = H;
+  while ((w > 1 || h > 1) && k < kMaxRangeLevels) {
+    ++k;
+    w = (w + 1) / 2;
+    h = (h + 1) / 2;
+    rp.w[k] = w;
+    rp.h[k] = h;
+    rp.off[k] = off;
+    off += w * h;
+  }
+  rp.nl = k;
+  rp.frame_texels = off;
+  return rp;
+}
+
+cudaError_t launch_range_pyr(const float* range, int F, int H, int W, RangePyr rp, float2* tex,
+                             cudaStream_t s) {
+  if (rp.nl < 1) return cudaSuccess;
+  k_rpyr_base<<<blocks_for(int64_t(F) * rp.w[1] * rp.h[1], 256), 256, 0, s>>>(range, F, H, W, rp, tex);
+  count_launches(1);
+  for (int k = 2; k <= rp.nl; ++k) {
+    k_rpyr_up<<<blocks_for(int64_t(F) * rp.w[k] * rp.h[k], 256), 256, 0, s>>>(F, k, rp, tex);
+    count_launches(1);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_range_map(float* depth, const Cam* cams, int F, int H, int W, cudaStream_t s) {

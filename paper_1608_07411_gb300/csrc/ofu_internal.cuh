@@ -347,8 +347,25 @@ cudaError_t launch_range_map(float* depth, const Cam* cams, int F, int H, int W,
 // Median field at finest-voxel centres (Morton order), then the Eq. 2 min/max
 // pyramid and the per-voxel leaf flags.  launch_dense_u0 needs a queue of
 // 8^D entries and a device counter as scratch.
+// Min / max pyramid of the range maps, used by the median scan to classify a
+// block of voxel centres against a whole frame at once.  Level k (1..nl) of a
+// frame has w[k] x h[k] texels; texel (x, y) holds the min and the max, over
+// the image's pixels in [x 2^k, (x + 1) 2^k) x [y 2^k, (y + 1) 2^k), of the
+// range where it is valid (> 0) and -inf where it is not.  Level 0 is the
+// range map itself.
+constexpr int kMaxRangeLevels = 24;
+struct RangePyr {
+  const float2* tex;
+  int64_t frame_texels;  // texels of one frame (levels 1..nl)
+  int nl;
+  int off[kMaxRangeLevels + 1], w[kMaxRangeLevels + 1], h[kMaxRangeLevels + 1];
+};
+// Level sizes and offsets for H x W maps (tex = nullptr).
+RangePyr range_pyr_dims(int H, int W);
+cudaError_t launch_range_pyr(const float* range, int F, int H, int W, RangePyr rp, float2* tex,
+                             cudaStream_t s);
 cudaError_t launch_dense_u0(const float* depth, const Cam* cams, int F, int H, int W, Geo g,
-                            double* u0, uint32_t* queue, unsigned long long* nqueue,
+                            RangePyr rp, double* u0, uint32_t* queue, unsigned long long* nqueue,
                             cudaStream_t s);
 cudaError_t launch_pyramid(const double* u0, int D, double* mn, double* mx, cudaStream_t s);
 cudaError_t launch_leaf_flags(const double* mn, const double* mx, int D, double spread_tau,
