@@ -120,7 +120,7 @@ void free_leaves(ofu_ctx* ctx, Leaves& L) {
   for (void* q : {static_cast<void*>(L.key), static_cast<void*>(L.level), static_cast<void*>(L.u),
                   static_cast<void*>(L.ubar), static_cast<void*>(L.p), static_cast<void*>(L.tau),
                   static_cast<void*>(L.sigma), static_cast<void*>(L.nbr),
-                  static_cast<void*>(L.soff), static_cast<void*>(L.ovf)})
+                  static_cast<void*>(L.soff), static_cast<void*>(L.khint), static_cast<void*>(L.ovf)})
     dfree(ctx, q);
   L = Leaves{};
 }
@@ -139,6 +139,7 @@ ofu_status ensure_leaves(ofu_ctx* ctx, int which, int64_t need) {
   CU(dalloc(ctx, &L.sigma, cap * sizeof(float)));
   CU(dalloc(ctx, &L.nbr, 6 * cap * sizeof(int32_t)));
   CU(dalloc(ctx, &L.soff, (cap + 1) * sizeof(uint32_t)));
+  CU(dalloc(ctx, &L.khint, cap * sizeof(uint16_t)));
   L.cap = cap;
   return OFU_OK;
 }
@@ -350,6 +351,9 @@ ofu_status rebuild_map(ofu_ctx* ctx) {
 ofu_status rebuild_topology(ofu_ctx* ctx, const uint32_t* samples_total = nullptr,
                             Carry carry = Carry{}) {
   const int64_t n = ctx->n;
+  // new leaves: no prox hint yet (0xffff is clamped to W, i.e. a full search)
+  CU(cudaMemsetAsync(ctx->L[ctx->cur].khint, 0xff, size_t(std::max<int64_t>(n, 1)) * sizeof(uint16_t),
+                     ctx->stream));
   ST(rebuild_map(ctx));
   uint32_t* ovfc;
   uint32_t* tmp;
@@ -668,13 +672,13 @@ ofu_status ofu_iterate(ofu_ctx* ctx, int32_t n) {
     CU(launch_dual(v, L.ubar, L.p, L.sigma, float(ctx->prm.lambda), dual_sets(ctx), ctx->stream));
     if (rec) CU(cudaEventRecord(ev[1], ctx->stream));
     CU(launch_primal(v, L.u, L.ubar, L.p, L.tau, L.soff, ctx->samp[ctx->cur], h16,
-                     float(ctx->prm.gamma), primal_sets(ctx), ctx->stream));
+                     float(ctx->prm.gamma), L.khint, primal_sets(ctx), ctx->stream));
     if (rec) {
       CU(cudaEventRecord(ev[2], ctx->stream));
       ctx->prof_launches[0] += 1;
       ctx->prof_launches[1] += 1;
       ctx->prof_bytes[0] += 45.0 * double(ctx->n);
-      ctx->prof_bytes[1] += 57.0 * double(ctx->n) + double(ctx->n_samples) * double(sample_bytes(ctx));
+      ctx->prof_bytes[1] += 93.0 * double(ctx->n);
     }
   }
   return OFU_OK;

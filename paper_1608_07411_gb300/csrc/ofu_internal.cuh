@@ -196,6 +196,7 @@ struct Leaves {
   float* sigma = nullptr;
   int32_t* nbr = nullptr;  // [6][cap]
   uint32_t* soff = nullptr;  // [cap + 1]
+  uint16_t* khint = nullptr;  // rank k* of the last prox of each leaf (a search hint only)
   int32_t* ovf = nullptr;  // finer-neighbour lists of nbr
   int64_t ovf_cap = 0;
 };
@@ -445,7 +446,7 @@ cudaError_t launch_dual_init(View v, const float* u, float* p, float lambda, flo
                              LeafSets ls, cudaStream_t s);
 cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const float* tau,
                           const uint32_t* soff, const void* samp, bool fp16, float gamma,
-                          LeafSets ls, cudaStream_t s);
+                          uint16_t* khint, LeafSets ls, cudaStream_t s);
 // SMs of the current device (looked up once per process; build.cu).
 int sm_count();
 size_t energy_tmp_bytes(int64_t n);

@@ -76,9 +76,8 @@ constexpr int kPrimalListLanes = 2;
 constexpr int kHeavyLanes = 32;
 // Slots a lane of the primal step loads per round (registers allow 2 there).
 constexpr int kPrimalSlotBatch = 2;
-// Leaves per thread of the dual and primal steps' light paths.
+// Leaves per thread of the dual step's light path.
 constexpr int kDualLightLeaves = 2;
-constexpr int kPrimalLightLeaves = 1;
 
 // Blocks of the heavy segment (kHeavyLanes lanes per heavy leaf).
 __device__ __host__ __forceinline__ int heavy_blocks(const Segments& sg) {
@@ -278,118 +277,107 @@ __device__ __forceinline__ void primal_group(const View& v, float* __restrict__ 
 // samples sorted it is clamp(b_k*, f_(k*-1), f_k*) (0-based f, f_-1 = -inf,
 // f_W = +inf) where k* is the number of k with f_k < b_k = v + t (W - 2k).
 // That predicate holds exactly for a prefix of k (f rises, b falls, and the
-// rounded b_k still falls), so k* is found by bisection in ceil(log2(W + 1))
-// probes (primal_light), or by a group search over G lanes (prox_l1_group).
-// The last probe that held is f_(k*-1), the last that failed is f_k*, so no
-// sample is loaded twice.
+// rounded b_k still falls), so k* is the unique rank where it turns false,
+// and any search that keeps [lo, hi] around it with f_(lo-1) (a rank that
+// held) and f_hi (a rank that failed) ends with the same k* and the same
+// two samples: the result does not depend on the search order.
 //
-// Primal step of the light path: K leaves per thread (a block covers K runs
-// of kThreads consecutive leaves), single entries only.  The loads of all K
-// leaves are issued before their gathers, and the K bisections of the prox
-// run in lock step, so each round has K independent sample loads in flight.
-// A thread past the end re-reads the last leaf and writes nothing; a list
-// leaf's lane gathers its own p (harmless) and writes nothing.
-template <int K, typename T>
+// Primal step of the light path: a thread per leaf, single entries only.  The
+// search starts from the leaf's k* of the previous iteration (khint): it
+// tests ranks k - 1 and k first (two loads of adjacent samples, issued
+// together), which settles k* at once whenever it has not moved -- nearly
+// always once the field has settled -- and otherwise bisects the side that
+// remains.  A thread past the end re-reads the last leaf and writes nothing;
+// a list leaf's lane gathers its own p (harmless) and writes nothing.
+template <typename T>
 __device__ __forceinline__ void primal_light(const View& v, float* __restrict__ u,
                                              float* __restrict__ ubar, const float* __restrict__ p,
                                              const float* __restrict__ tau,
                                              const uint32_t* __restrict__ soff,
-                                             const T* __restrict__ samp, float gamma, int b) {
+                                             const T* __restrict__ samp, float gamma,
+                                             uint16_t* __restrict__ khint, int b) {
   const size_t st = size_t(v.stride);
-  const int64_t base = int64_t(b) * (kThreads * K) + threadIdx.x;
-  int64_t l[K];
-  int32_t e[K][6];
-  int lev[K], W[K];
-  float q[K][3], tl[K], ul[K];
-  uint32_t o[K];
+  const int64_t l = int64_t(b) * kThreads + threadIdx.x;
+  const int64_t lc = l < v.n ? l : v.n - 1;
+  int32_t e[6];
 #pragma unroll
-  for (int j = 0; j < K; ++j) {
-    l[j] = base + j * kThreads;
-    const int64_t lc = l[j] < v.n ? l[j] : v.n - 1;
-#pragma unroll
-    for (int f = 0; f < 6; ++f) e[j][f] = v.nbr[f * st + lc];
-    lev[j] = v.level[lc];
-    tl[j] = tau[lc];
-    o[j] = soff[lc];
-    W[j] = int(soff[lc + 1] - o[j]);
-  }
+  for (int f = 0; f < 6; ++f) e[f] = v.nbr[f * st + lc];
+  const int lev = v.level[lc];
+  const float tl = tau[lc];
+  const uint32_t o = soff[lc];
+  const int W = int(soff[lc + 1] - o);
   // the structure arrays above are read before the previous kernel ends;
-  // u and p only after it
+  // u, p and the hint only after it
   grid_dep_wait();
   grid_dep_launch();
-  float pn[K][3];
+  const float ul = u[lc];
+  float q[3], pn[3];
 #pragma unroll
-  for (int j = 0; j < K; ++j) {
-    const int64_t lc = l[j] < v.n ? l[j] : v.n - 1;
-    ul[j] = u[lc];
+  for (int d = 0; d < 3; ++d) q[d] = p[d * st + lc];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) q[j][d] = p[d * st + lc];
+  for (int d = 0; d < 3; ++d) pn[d] = p[d * st + (e[3 + d] >= 0 ? entry_idx(e[3 + d]) : 0u)];
+  const int kh = min(int(khint[lc]), W);
+  const float h = edge_f(v.D, lev);
+  float dv = 0.0f;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) pn[j][d] = p[d * st + (e[j][3 + d] >= 0 ? entry_idx(e[j][3 + d]) : 0u)];
+  for (int d = 0; d < 3; ++d) {
+    const float hm = edge_f(v.D, e[d] >= 0 ? entry_level(e[d]) : lev);
+    dv += (e[d] >= 0 ? inv_delta(h, hm) : 0.0f) * q[d];
   }
-  // prox argument x, scaled weight t and the bisection state [lo, hi) per leaf
-  float x[K], t[K], flo[K], fhi[K];
-  int lo[K], hi[K];
 #pragma unroll
-  for (int j = 0; j < K; ++j) {
-    const float h = edge_f(v.D, lev[j]);
-    float dv = 0.0f;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const float hm = edge_f(v.D, e[j][d] >= 0 ? entry_level(e[j][d]) : lev[j]);
-      dv += (e[j][d] >= 0 ? inv_delta(h, hm) : 0.0f) * q[j][d];
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      // same or coarser n: (h_n^3 / h^3) (h / h_n)^2 / Delta = (h_n / h) / Delta
-      const float hn = edge_f(v.D, e[j][3 + d] >= 0 ? entry_level(e[j][3 + d]) : lev[j]);
-      dv -= e[j][3 + d] >= 0 ? (hn / h) * inv_delta(h, hn) * pn[j][d] : 0.0f;
-    }
-    bool skip = l[j] >= v.n;
-#pragma unroll
-    for (int f = 0; f < 6; ++f) skip |= is_list(e[j][f]);
-    if (skip) l[j] = -1;
-    x[j] = ul[j] + tl[j] * dv;
-    t[j] = tl[j] / (float(W[j]) + gamma);
-    lo[j] = 0;
-    hi[j] = skip ? 0 : W[j];
-    flo[j] = -CUDART_INF_F;
-    fhi[j] = CUDART_INF_F;
+  for (int d = 0; d < 3; ++d) {
+    // same or coarser n: (h_n^3 / h^3) (h / h_n)^2 / Delta = (h_n / h) / Delta
+    const float hn = edge_f(v.D, e[3 + d] >= 0 ? entry_level(e[3 + d]) : lev);
+    dv -= e[3 + d] >= 0 ? (hn / h) * inv_delta(h, hn) * pn[d] : 0.0f;
   }
-  // the bisection for the K leaves at once
-  for (;;) {
-    bool any = false;
+  bool skip = l >= v.n;
 #pragma unroll
-    for (int j = 0; j < K; ++j) any |= lo[j] < hi[j];
-    if (!any) break;
-    float fm[K];
-    int mid[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      mid[j] = (lo[j] + hi[j]) >> 1;
-      fm[j] = lo[j] < hi[j] ? load_sample(samp + o[j], mid[j]) : 0.0f;
+  for (int f = 0; f < 6; ++f) skip |= is_list(e[f]);
+  const float x = ul + tl * dv;
+  const float t = tl / (float(W) + gamma);
+  const T* fs = samp + o;
+  // search state: k* in [lo, hi]; flo = f_(lo-1) when lo > 0, fhi = f_hi when hi < W
+  int lo = 0, hi = skip ? 0 : W;
+  float flo = -CUDART_INF_F, fhi = CUDART_INF_F;
+  if (!skip) {
+    const float fa = kh > 0 ? load_sample(fs, kh - 1) : 0.0f;
+    const float fb = kh < W ? load_sample(fs, kh) : 0.0f;
+    if (kh > 0) {
+      if (fa < __fmaf_rn(t, float(W - 2 * (kh - 1)), x)) {
+        lo = kh;
+        flo = fa;
+      } else {
+        hi = kh - 1;
+        fhi = fa;
+      }
     }
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      if (lo[j] < hi[j]) {
-        if (fm[j] < __fmaf_rn(t[j], float(W[j] - 2 * mid[j]), x[j])) {
-          lo[j] = mid[j] + 1;
-          flo[j] = fm[j];
-        } else {
-          hi[j] = mid[j];
-          fhi[j] = fm[j];
-        }
+    if (kh < W && lo <= kh && kh < hi) {
+      if (fb < __fmaf_rn(t, float(W - 2 * kh), x)) {
+        lo = kh + 1;
+        flo = fb;
+      } else {
+        hi = kh;
+        fhi = fb;
       }
     }
   }
-#pragma unroll
-  for (int j = 0; j < K; ++j) {
-    if (l[j] < 0) continue;
-    const float bk = __fmaf_rn(t[j], float(W[j] - 2 * lo[j]), x[j]);
-    const float un = fminf(fmaxf(fmaxf(flo[j], fminf(bk, fhi[j])), -1.0f), 1.0f);
-    u[l[j]] = un;
-    ubar[l[j]] = 2.0f * un - ul[j];
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const float fm = load_sample(fs, mid);
+    if (fm < __fmaf_rn(t, float(W - 2 * mid), x)) {
+      lo = mid + 1;
+      flo = fm;
+    } else {
+      hi = mid;
+      fhi = fm;
+    }
   }
+  if (skip) return;
+  const float bk = __fmaf_rn(t, float(W - 2 * lo), x);
+  const float un = fminf(fmaxf(fmaxf(flo, fminf(bk, fhi)), -1.0f), 1.0f);
+  u[l] = un;
+  ubar[l] = 2.0f * un - ul;
+  khint[l] = uint16_t(lo);
 }
 
 template <typename T>
@@ -399,7 +387,9 @@ __global__ void __launch_bounds__(kThreads, kIterMinBlocks) k_primal(View v, flo
                                                                      const float* __restrict__ tau,
                                                                      const uint32_t* __restrict__ soff,
                                                                      const T* __restrict__ samp,
-                                                                     float gamma, Segments sg) {
+                                                                     float gamma,
+                                                                     uint16_t* __restrict__ khint,
+                                                                     Segments sg) {
   const int hb = heavy_blocks(sg);
   const int lb = (sg.n_list * kPrimalListLanes + kThreads - 1) / kThreads;
   const int b = int(blockIdx.x);
@@ -413,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, kIterMinBlocks) k_primal(View v, flo
                                      b - hb);
     return;
   }
-  primal_light<kPrimalLightLeaves>(v, u, ubar, p, tau, soff, samp, gamma, b - (hb + lb));
+  primal_light(v, u, ubar, p, tau, soff, samp, gamma, khint, b - (hb + lb));
 }
 
 // ---------------------------------------------------------------------------
@@ -862,15 +852,15 @@ cudaError_t launch_dual_init(View v, const float* u, float* p, float lambda, flo
 
 cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const float* tau,
                           const uint32_t* soff, const void* samp, bool fp16, float gamma,
-                          LeafSets ls, cudaStream_t s) {
+                          uint16_t* khint, LeafSets ls, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
   const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
-  const unsigned nb = grid_of(v.n, sg, kPrimalListLanes, kPrimalLightLeaves);
+  const unsigned nb = grid_of(v.n, sg, kPrimalListLanes, 1);
   const cudaError_t e =
       fp16 ? launch_iter(k_primal<__half>, nb, s, v, u, ubar, p, tau, soff,
-                         reinterpret_cast<const __half*>(samp), gamma, sg)
+                         reinterpret_cast<const __half*>(samp), gamma, khint, sg)
            : launch_iter(k_primal<float>, nb, s, v, u, ubar, p, tau, soff,
-                         reinterpret_cast<const float*>(samp), gamma, sg);
+                         reinterpret_cast<const float*>(samp), gamma, khint, sg);
   count_launches(1);
   return e;
 }
