@@ -224,6 +224,19 @@ struct LeafSets {
   int n_list = 0;
 };
 
+// Divergence records of the primal step's heavy and list leaves, rebuilt with
+// the leaf classes (solve.cu).  Group position g runs over the heavy set, then
+// the list set.  The -face neighbours of position g are the records
+// start[g] .. start[g + 1] - 1: rec = neighbour index | axis << 28, w = its
+// weight (h_n^3 / h^3) alpha_nl / Delta; cp[3 g + d] is the sum of
+// alpha / Delta over the neighbours across the +d face.
+struct DivRecs {
+  const uint32_t* start = nullptr;
+  const uint32_t* rec = nullptr;
+  const float* w = nullptr;
+  const float* cp = nullptr;
+};
+
 // The structure before a split/join pass, handed to the neighbour build of
 // the new one: a kept leaf (same key, same level) whose neighbours across a
 // face were all kept has the same neighbours afterwards, so its entry is
@@ -446,7 +459,14 @@ cudaError_t launch_dual_init(View v, const float* u, float* p, float lambda, flo
                              LeafSets ls, cudaStream_t s);
 cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const float* tau,
                           const uint32_t* soff, const void* samp, bool fp16, float gamma,
-                          uint16_t* khint, LeafSets ls, cudaStream_t s);
+                          uint16_t* khint, LeafSets ls, DivRecs dr, cudaStream_t s);
+// Divergence records of the primal leaf sets: counts per group position
+// (cnt[0 .. n_heavy + n_list)), then, with start = their exclusive scan, the
+// records.  rec / w need at least the scanned total, which is at most the
+// list entries plus three per group leaf.
+cudaError_t launch_div_count(View v, LeafSets ls, uint32_t* cnt, cudaStream_t s);
+cudaError_t launch_div_fill(View v, LeafSets ls, const uint32_t* start, uint32_t* rec, float* w,
+                            float* cp, cudaStream_t s);
 // SMs of the current device (looked up once per process; build.cu).
 int sm_count();
 size_t energy_tmp_bytes(int64_t n);

@@ -74,8 +74,6 @@ constexpr int kDualListLanes = 4;
 constexpr int kPrimalListLanes = 2;
 // Lanes per heavy leaf (a face list longer than kHeavy): one warp.
 constexpr int kHeavyLanes = 32;
-// Slots a lane of the primal step loads per round (registers allow 2 there).
-constexpr int kPrimalSlotBatch = 2;
 // Leaves per thread of the dual step's light path.
 constexpr int kDualLightLeaves = 2;
 
@@ -185,93 +183,6 @@ __global__ void __launch_bounds__(kThreads, kIterMinBlocks) k_dual(View v, const
   }
 }
 
-// Divergence of p at leaf l over its six faces' slots, this lane's share of
-// a group of G lanes: +faces weigh p(l) by alpha / Delta per neighbour,
-// -faces subtract (h_n^3 / h^3) alpha_nl / Delta p(n).
-__device__ __forceinline__ float div_share(const View& v, const float* __restrict__ p, int64_t l,
-                                           const int32_t e[6], float h, const float q[3], int lane,
-                                           int G) {
-  float acc = 0.0f;
-  for_each_slot<6, kPrimalSlotBatch>(v, e, lane, G, [&](int f, int32_t ent) {
-    const float hm = edge_f(v.D, entry_level(ent));
-    if (f < 3) {
-      acc += plus_weight(h, hm) * (f == 0 ? q[0] : (f == 1 ? q[1] : q[2]));
-    } else {
-      acc -= minus_weight(h, hm) * p[int64_t(f - 3) * v.stride + entry_idx(ent)];
-    }
-  });
-  return acc;
-}
-
-// The prox of the data term (described at primal_light) found by a group of
-// G lanes: each round the lanes test G evenly spaced ranks of [lo, hi) and the
-// count of those that hold (a prefix, the predicate being monotone) narrows
-// the range, so a leaf of W samples takes about log_G(W) rounds of
-// independent loads.  k* is the same as the bisection's, hence so is the
-// result, in every lane.  The count is a warp ballot (every lane of the warp
-// takes part in every round).
-template <int G, typename T>
-__device__ __forceinline__ float prox_l1_group(const T* __restrict__ f, int W, float v, float t,
-                                               int lane) {
-  static_assert(G >= 1 && G <= 32 && (G & (G - 1)) == 0, "G lanes of one warp");
-  constexpr unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
-  const unsigned gshift = (threadIdx.x & 31u) & ~unsigned(G - 1);
-  int lo = 0, hi = W;
-  for (;;) {
-    const bool active = lo < hi;
-    if (!__any_sync(kFull, active)) break;
-    const int step = active ? (hi - lo + G - 1) / G : 0;
-    const int q = lo + lane * step;
-    const bool ok = active && q < hi && load_sample(f, q) < __fmaf_rn(t, float(W - 2 * q), v);
-    const int c = __popc((__ballot_sync(kFull, ok) >> gshift) & gmask);
-    if (active) {
-      if (c == 0) {
-        hi = lo;
-      } else {
-        const int last = lo + (c - 1) * step;   // the last rank that holds
-        hi = min(hi, lo + c * step);             // the first that fails, if tested
-        lo = last + 1;
-      }
-    }
-  }
-  const float flo = lo > 0 ? load_sample(f, lo - 1) : -CUDART_INF_F;
-  const float fhi = lo < W ? load_sample(f, lo) : CUDART_INF_F;
-  const float b = __fmaf_rn(t, float(W - 2 * lo), v);
-  return fmaxf(flo, fminf(b, fhi));
-}
-
-// A primal step of the leaves of a compacted set, G lanes per leaf (layout
-// as dual_group): the divergence over the slots and the prox by group search.
-template <int G, typename T>
-__device__ __forceinline__ void primal_group(const View& v, float* __restrict__ u,
-                                             float* __restrict__ ubar, const float* __restrict__ p,
-                                             const float* __restrict__ tau,
-                                             const uint32_t* __restrict__ soff,
-                                             const T* __restrict__ samp, float gamma,
-                                             const uint32_t* __restrict__ set, int n_set, int b) {
-  const int t = b * kThreads + int(threadIdx.x);
-  const int j = t / G, lane = t % G;
-  const bool valid = j < n_set;
-  const int64_t l = set[valid ? j : n_set - 1];
-  int32_t e[6];
-#pragma unroll
-  for (int f = 0; f < 6; ++f) e[f] = v.nbr[int64_t(f) * v.stride + l];
-  const float h = edge_f(v.D, v.level[l]);
-  float q[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) q[d] = p[int64_t(d) * v.stride + l];
-  const uint32_t o = soff[l];
-  const int W = int(soff[l + 1] - o);
-  const float ul = u[l];
-  const float tl = tau[l];
-  const float dv = group_sum<G>(div_share(v, p, l, e, h, q, lane, G));
-  float un = prox_l1_group<G>(samp + o, W, ul + tl * dv, tl / (float(W) + gamma), lane);
-  if (lane != 0 || !valid) return;
-  un = fminf(fmaxf(un, -1.0f), 1.0f);
-  u[l] = un;
-  ubar[l] = 2.0f * un - ul;
-}
-
 // Prox of the data term: argmin_x (x - v)^2 / (2 tau) + c sum_k |x - f_k| is
 // the median of {f_k} and {v + t (W - 2k)}_{k=0..W}, t = tau c.  With the
 // samples sorted it is clamp(b_k*, f_(k*-1), f_k*) (0-based f, f_-1 = -inf,
@@ -282,13 +193,56 @@ __device__ __forceinline__ void primal_group(const View& v, float* __restrict__ 
 // held) and f_hi (a rank that failed) ends with the same k* and the same
 // two samples: the result does not depend on the search order.
 //
-// Primal step of the light path: a thread per leaf, single entries only.  The
-// search starts from the leaf's k* of the previous iteration (khint): it
-// tests ranks k - 1 and k first (two loads of adjacent samples, issued
-// together), which settles k* at once whenever it has not moved -- nearly
-// always once the field has settled -- and otherwise bisects the side that
-// remains.  A thread past the end re-reads the last leaf and writes nothing;
-// a list leaf's lane gathers its own p (harmless) and writes nothing.
+// The prox from the search hint kh (the leaf's k* of the previous
+// iteration): ranks kh - 1 and kh are tested first (two loads of adjacent
+// samples, issued together), which settles k* at once whenever it has not
+// moved -- nearly always once the field has settled -- and otherwise the
+// side that remains is bisected.  Returns the prox (before the clamp to
+// [-1, 1]) and k*.
+template <typename T>
+__device__ __forceinline__ float prox_hinted(const T* __restrict__ fs, int W, float x, float t, int kh,
+                                             int* kstar) {
+  int lo = 0, hi = W;
+  float flo = -CUDART_INF_F, fhi = CUDART_INF_F;
+  const float fa = kh > 0 ? load_sample(fs, kh - 1) : 0.0f;
+  const float fb = kh < W ? load_sample(fs, kh) : 0.0f;
+  if (kh > 0) {
+    if (fa < __fmaf_rn(t, float(W - 2 * (kh - 1)), x)) {
+      lo = kh;
+      flo = fa;
+    } else {
+      hi = kh - 1;
+      fhi = fa;
+    }
+  }
+  if (kh < W && lo <= kh && kh < hi) {
+    if (fb < __fmaf_rn(t, float(W - 2 * kh), x)) {
+      lo = kh + 1;
+      flo = fb;
+    } else {
+      hi = kh;
+      fhi = fb;
+    }
+  }
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const float fm = load_sample(fs, mid);
+    if (fm < __fmaf_rn(t, float(W - 2 * mid), x)) {
+      lo = mid + 1;
+      flo = fm;
+    } else {
+      hi = mid;
+      fhi = fm;
+    }
+  }
+  *kstar = lo;
+  return fmaxf(flo, fminf(__fmaf_rn(t, float(W - 2 * lo), x), fhi));
+}
+
+// Primal step of the light path: a thread per leaf, single entries only, the
+// prox by prox_hinted.  A thread past the end re-reads the last leaf and
+// writes nothing; a list leaf's lane gathers its own p (harmless) and writes
+// nothing.
 template <typename T>
 __device__ __forceinline__ void primal_light(const View& v, float* __restrict__ u,
                                              float* __restrict__ ubar, const float* __restrict__ p,
@@ -335,49 +289,136 @@ __device__ __forceinline__ void primal_light(const View& v, float* __restrict__ 
   for (int f = 0; f < 6; ++f) skip |= is_list(e[f]);
   const float x = ul + tl * dv;
   const float t = tl / (float(W) + gamma);
-  const T* fs = samp + o;
-  // search state: k* in [lo, hi]; flo = f_(lo-1) when lo > 0, fhi = f_hi when hi < W
-  int lo = 0, hi = skip ? 0 : W;
-  float flo = -CUDART_INF_F, fhi = CUDART_INF_F;
-  if (!skip) {
-    const float fa = kh > 0 ? load_sample(fs, kh - 1) : 0.0f;
-    const float fb = kh < W ? load_sample(fs, kh) : 0.0f;
-    if (kh > 0) {
-      if (fa < __fmaf_rn(t, float(W - 2 * (kh - 1)), x)) {
-        lo = kh;
-        flo = fa;
-      } else {
-        hi = kh - 1;
-        fhi = fa;
-      }
-    }
-    if (kh < W && lo <= kh && kh < hi) {
-      if (fb < __fmaf_rn(t, float(W - 2 * kh), x)) {
-        lo = kh + 1;
-        flo = fb;
-      } else {
-        hi = kh;
-        fhi = fb;
-      }
-    }
-  }
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    const float fm = load_sample(fs, mid);
-    if (fm < __fmaf_rn(t, float(W - 2 * mid), x)) {
-      lo = mid + 1;
-      flo = fm;
-    } else {
-      hi = mid;
-      fhi = fm;
-    }
-  }
+  int ks = 0;
+  const float pr = skip ? 0.0f : prox_hinted(samp + o, W, x, t, kh, &ks);
   if (skip) return;
-  const float bk = __fmaf_rn(t, float(W - 2 * lo), x);
-  const float un = fminf(fmaxf(fmaxf(flo, fminf(bk, fhi)), -1.0f), 1.0f);
+  const float un = fminf(fmaxf(pr, -1.0f), 1.0f);
   u[l] = un;
   ubar[l] = 2.0f * un - ul;
-  khint[l] = uint16_t(lo);
+  khint[l] = uint16_t(ks);
+}
+
+// Records a lane loads before the wait (G lanes per leaf cover G times this
+// many -face neighbours in the first round).
+constexpr int kDivRecBatch = 4;
+
+// A primal step of the leaves of a compacted set (heavy or list leaves), G
+// lanes per leaf: the j-th leaf of `set` (group position g0 + j) for threads
+// j G .. j G + G - 1 of the segment starting at block 0 + `b`.  The leaf's
+// -face neighbours come from its divergence records, static between
+// restructures and so read before the wait together with the +face weight
+// sums; after it the lanes gather p at the neighbours, the group sums, and
+// lane 0 runs the prox search from the hint.  Lanes past the end take the
+// last leaf and do not write (every lane of the warp joins the shuffles).
+template <int G, typename T>
+__device__ __forceinline__ void primal_group(const View& v, float* __restrict__ u,
+                                             float* __restrict__ ubar, const float* __restrict__ p,
+                                             const float* __restrict__ tau,
+                                             const uint32_t* __restrict__ soff,
+                                             const T* __restrict__ samp, float gamma,
+                                             uint16_t* __restrict__ khint, const DivRecs& dr,
+                                             const uint32_t* __restrict__ set, int n_set, int g0,
+                                             int b) {
+  const size_t st = size_t(v.stride);
+  const int t = b * kThreads + int(threadIdx.x);
+  const int j = t / G, lane = t % G;
+  const bool valid = j < n_set;
+  const int jc = valid ? j : n_set - 1;
+  const int64_t l = set[jc];
+  const int g = g0 + jc;
+  const uint32_t m0 = dr.start[g], m1 = dr.start[g + 1];
+  float cp[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) cp[d] = dr.cp[3 * g + d];
+  const float tl = tau[l];
+  const uint32_t o = soff[l];
+  const int W = int(soff[l + 1] - o);
+  uint32_t rec[kDivRecBatch];
+  float w[kDivRecBatch];
+#pragma unroll
+  for (int r = 0; r < kDivRecBatch; ++r) {
+    const uint32_t k = m0 + lane + r * G;
+    rec[r] = k < m1 ? dr.rec[k] : 0u;
+    w[r] = k < m1 ? dr.w[k] : 0.0f;
+  }
+  grid_dep_wait();
+  grid_dep_launch();
+  float acc = 0.0f;
+#pragma unroll
+  for (int r = 0; r < kDivRecBatch; ++r)
+    acc += w[r] * p[size_t(rec[r] >> 28) * st + (rec[r] & 0x0fffffffu)];
+#pragma unroll 4
+  for (uint32_t k = m0 + lane + kDivRecBatch * G; k < m1; k += G) {
+    const uint32_t rk = dr.rec[k];
+    acc += dr.w[k] * p[size_t(rk >> 28) * st + (rk & 0x0fffffffu)];
+  }
+  acc = group_sum<G>(acc);
+  if (lane != 0 || !valid) return;
+  const float ul = u[l];
+  const float dv = cp[0] * p[l] + cp[1] * p[st + l] + cp[2] * p[2 * st + l] - acc;
+  int ks;
+  const float un = fminf(fmaxf(prox_hinted(samp + o, W, ul + tl * dv, tl / (float(W) + gamma),
+                                           min(int(khint[l]), W), &ks),
+                               -1.0f),
+                         1.0f);
+  u[l] = un;
+  ubar[l] = 2.0f * un - ul;
+  khint[l] = uint16_t(ks);
+}
+
+// Divergence records (see DivRecs): counts, then records and +face sums.
+__global__ void k_div_count(View v, LeafSets ls, uint32_t* __restrict__ cnt) {
+  const int g = int(blockIdx.x) * blockDim.x + int(threadIdx.x);
+  if (g >= ls.n_heavy + ls.n_list) return;
+  const int64_t l = g < ls.n_heavy ? ls.heavy[g] : ls.list[g - ls.n_heavy];
+  uint32_t c = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int32_t e = v.nbr[int64_t(3 + d) * v.stride + l];
+    c += e >= 0 ? 1u : (e == kEmpty ? 0u : uint32_t(v.ovf[list_start(e)]));
+  }
+  cnt[g] = c;
+}
+
+__global__ void k_div_fill(View v, LeafSets ls, const uint32_t* __restrict__ start,
+                           uint32_t* __restrict__ rec, float* __restrict__ w,
+                           float* __restrict__ cp) {
+  const int g = int(blockIdx.x) * blockDim.x + int(threadIdx.x);
+  if (g >= ls.n_heavy + ls.n_list) return;
+  const int64_t l = g < ls.n_heavy ? ls.heavy[g] : ls.list[g - ls.n_heavy];
+  const float h = edge_f(v.D, v.level[l]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int32_t e = v.nbr[int64_t(d) * v.stride + l];
+    float sum = 0.0f;
+    if (e >= 0) {
+      sum = plus_weight(h, edge_f(v.D, entry_level(e)));
+    } else if (e != kEmpty) {
+      const uint32_t s0 = list_start(e);
+      const int c = v.ovf[s0];
+      for (int k = 0; k < c; ++k) sum += plus_weight(h, edge_f(v.D, entry_level(v.ovf[s0 + 1 + k])));
+    }
+    cp[3 * g + d] = sum;
+  }
+  uint32_t k = start[g];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int32_t e = v.nbr[int64_t(3 + d) * v.stride + l];
+    if (e >= 0) {
+      rec[k] = entry_idx(e) | (uint32_t(d) << 28);
+      w[k] = minus_weight(h, edge_f(v.D, entry_level(e)));
+      ++k;
+    } else if (e != kEmpty) {
+      const uint32_t s0 = list_start(e);
+      const int c = v.ovf[s0];
+      for (int i = 0; i < c; ++i) {
+        const int32_t f = v.ovf[s0 + 1 + i];
+        rec[k] = entry_idx(f) | (uint32_t(d) << 28);
+        w[k] = minus_weight(h, edge_f(v.D, entry_level(f)));
+        ++k;
+      }
+    }
+  }
 }
 
 template <typename T>
@@ -389,18 +430,17 @@ __global__ void __launch_bounds__(kThreads, kIterMinBlocks) k_primal(View v, flo
                                                                      const T* __restrict__ samp,
                                                                      float gamma,
                                                                      uint16_t* __restrict__ khint,
-                                                                     Segments sg) {
+                                                                     Segments sg, DivRecs dr) {
   const int hb = heavy_blocks(sg);
   const int lb = (sg.n_list * kPrimalListLanes + kThreads - 1) / kThreads;
   const int b = int(blockIdx.x);
   if (b < hb + lb) {
-    grid_dep_wait();
-    grid_dep_launch();
     if (b < hb)
-      primal_group<kHeavyLanes>(v, u, ubar, p, tau, soff, samp, gamma, sg.heavy, sg.n_heavy, b);
+      primal_group<kHeavyLanes>(v, u, ubar, p, tau, soff, samp, gamma, khint, dr, sg.heavy,
+                                sg.n_heavy, 0, b);
     else
-      primal_group<kPrimalListLanes>(v, u, ubar, p, tau, soff, samp, gamma, sg.list, sg.n_list,
-                                     b - hb);
+      primal_group<kPrimalListLanes>(v, u, ubar, p, tau, soff, samp, gamma, khint, dr, sg.list,
+                                     sg.n_list, sg.n_heavy, b - hb);
     return;
   }
   primal_light(v, u, ubar, p, tau, soff, samp, gamma, khint, b - (hb + lb));
@@ -852,17 +892,34 @@ cudaError_t launch_dual_init(View v, const float* u, float* p, float lambda, flo
 
 cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const float* tau,
                           const uint32_t* soff, const void* samp, bool fp16, float gamma,
-                          uint16_t* khint, LeafSets ls, cudaStream_t s) {
+                          uint16_t* khint, LeafSets ls, DivRecs dr, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
   const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
   const unsigned nb = grid_of(v.n, sg, kPrimalListLanes, 1);
   const cudaError_t e =
       fp16 ? launch_iter(k_primal<__half>, nb, s, v, u, ubar, p, tau, soff,
-                         reinterpret_cast<const __half*>(samp), gamma, khint, sg)
+                         reinterpret_cast<const __half*>(samp), gamma, khint, sg, dr)
            : launch_iter(k_primal<float>, nb, s, v, u, ubar, p, tau, soff,
-                         reinterpret_cast<const float*>(samp), gamma, khint, sg);
+                         reinterpret_cast<const float*>(samp), gamma, khint, sg, dr);
   count_launches(1);
   return e;
+}
+
+cudaError_t launch_div_count(View v, LeafSets ls, uint32_t* cnt, cudaStream_t s) {
+  const int ng = ls.n_heavy + ls.n_list;
+  if (ng == 0) return cudaSuccess;
+  k_div_count<<<blocks_for(ng, kThreads), kThreads, 0, s>>>(v, ls, cnt);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_div_fill(View v, LeafSets ls, const uint32_t* start, uint32_t* rec, float* w,
+                            float* cp, cudaStream_t s) {
+  const int ng = ls.n_heavy + ls.n_list;
+  if (ng == 0) return cudaSuccess;
+  k_div_fill<<<blocks_for(ng, kThreads), kThreads, 0, s>>>(v, ls, start, rec, w, cp);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 size_t energy_tmp_bytes(int64_t) { return size_t(2 * kEnergyBlocks) * sizeof(double); }
