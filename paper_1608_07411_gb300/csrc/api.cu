@@ -32,7 +32,7 @@ enum Buf {
   B_SCAN, B_U0, B_PYR, B_FLAGS, B_POS, B_CNT, B_OVFC, B_CLS, B_OUTC, B_JL, B_SRC, B_LIST,
   B_SMALL, B_PART, B_BIG, B_LONGQ, B_FWD, B_AUX, B_FULL, B_PENDQ, B_Q, B_QF, B_QD, B_QT, B_LFL,
   B_MG, B_MC, B_MN, B_MV, B_MT, B_FTC, B_FTT, B_FTL, B_FTH, B_RPYR, B_DRS, B_DRR, B_DRW, B_DRC,
-  B_NUM
+  B_GRS, B_GRR, B_GRW, B_NUM
 };
 
 struct Bufs {
@@ -420,31 +420,36 @@ ofu_status rebuild_topology(ofu_ctx* ctx, const uint32_t* samples_total = nullpt
   v = view_of(ctx);
   CU(launch_precond(v, carry, L.tau, L.sigma, ctx->heavy + ctx->heavy_cap, ctx->n_heavy_primal,
                     ctx->stream));
-  // divergence records of the primal step's heavy and list leaves: at most
+  // neighbour records of the heavy and list leaves (the dual step's +face
+  // gradient records, the primal step's -face divergence records): at most
   // every list entry plus three single neighbours per leaf, so no read-back
-  const LeafSets ps = primal_sets(ctx);
-  const int64_t ng = int64_t(ps.n_heavy) + ps.n_list;
-  uint32_t *dstart, *drec;
-  float *dw, *dcp;
-  ST(ensure(ctx, B_DRS, size_t(ng + 1), &dstart));
-  ST(ensure(ctx, B_DRR, size_t(total) + 3 * size_t(ng) + 1, &drec));
-  ST(ensure(ctx, B_DRW, size_t(total) + 3 * size_t(ng) + 1, &dw));
-  ST(ensure(ctx, B_DRC, 3 * size_t(ng) + 1, &dcp));
-  if (ng > 0) {
-    CU(launch_div_count(v, ps, dstart, ctx->stream));
-    CU(scan_exclusive<uint32_t>(dstart, dstart, ng, tmp, ctx->stream));
-    CU(launch_div_fill(v, ps, dstart, drec, dw, dcp, ctx->stream));
+  for (int plus = 0; plus < 2; ++plus) {
+    const LeafSets ls = plus ? dual_sets(ctx) : primal_sets(ctx);
+    const int64_t ng = int64_t(ls.n_heavy) + ls.n_list;
+    uint32_t *rstart, *rrec;
+    float *rw, *rcp = nullptr;
+    ST(ensure(ctx, plus ? B_GRS : B_DRS, size_t(ng + 1), &rstart));
+    ST(ensure(ctx, plus ? B_GRR : B_DRR, size_t(total) + 3 * size_t(ng) + 1, &rrec));
+    ST(ensure(ctx, plus ? B_GRW : B_DRW, size_t(total) + 3 * size_t(ng) + 1, &rw));
+    if (!plus) ST(ensure(ctx, B_DRC, 3 * size_t(ng) + 1, &rcp));
+    if (ng > 0) {
+      CU(launch_recs_count(v, ls, plus != 0, rstart, ctx->stream));
+      CU(scan_exclusive<uint32_t>(rstart, rstart, ng, tmp, ctx->stream));
+      CU(launch_recs_fill(v, ls, plus != 0, rstart, rrec, rw, rcp, ctx->stream));
+    }
   }
   return OFU_OK;
 }
 
-DivRecs div_recs(ofu_ctx* ctx) {
+// The records built by rebuild_topology (gradient: the dual step's sets;
+// divergence: the primal step's).
+NbrRecs nbr_recs(ofu_ctx* ctx, bool gradient) {
   Bufs& B = bufs(ctx);
-  DivRecs d;
-  d.start = static_cast<const uint32_t*>(B.p[B_DRS]);
-  d.rec = static_cast<const uint32_t*>(B.p[B_DRR]);
-  d.w = static_cast<const float*>(B.p[B_DRW]);
-  d.cp = static_cast<const float*>(B.p[B_DRC]);
+  NbrRecs d;
+  d.start = static_cast<const uint32_t*>(B.p[gradient ? B_GRS : B_DRS]);
+  d.rec = static_cast<const uint32_t*>(B.p[gradient ? B_GRR : B_DRR]);
+  d.w = static_cast<const float*>(B.p[gradient ? B_GRW : B_DRW]);
+  d.cp = gradient ? nullptr : static_cast<const float*>(B.p[B_DRC]);
   return d;
 }
 
@@ -695,10 +700,11 @@ ofu_status ofu_iterate(ofu_ctx* ctx, int32_t n) {
       ctx->prof_used += 3;
       CU(cudaEventRecord(ev[0], ctx->stream));
     }
-    CU(launch_dual(v, L.ubar, L.p, L.sigma, float(ctx->prm.lambda), dual_sets(ctx), ctx->stream));
+    CU(launch_dual(v, L.ubar, L.p, L.sigma, float(ctx->prm.lambda), dual_sets(ctx),
+                   nbr_recs(ctx, true), ctx->stream));
     if (rec) CU(cudaEventRecord(ev[1], ctx->stream));
     CU(launch_primal(v, L.u, L.ubar, L.p, L.tau, L.soff, ctx->samp[ctx->cur], h16,
-                     float(ctx->prm.gamma), L.khint, primal_sets(ctx), div_recs(ctx), ctx->stream));
+                     float(ctx->prm.gamma), L.khint, primal_sets(ctx), nbr_recs(ctx, false), ctx->stream));
     if (rec) {
       CU(cudaEventRecord(ev[2], ctx->stream));
       ctx->prof_launches[0] += 1;
@@ -1321,7 +1327,7 @@ ofu_status ofu_warm_start(ofu_ctx* ctx, const ofu_mlp* net) {
                      ctx->stream));
   // dual start consistent with the new field: lambda n on its edges
   CU(launch_dual_init(view_of(ctx), L.u, L.p, float(ctx->prm.lambda), kWarmEdge, dual_sets(ctx),
-                      ctx->stream));
+                      nbr_recs(ctx, true), ctx->stream));
   return OFU_OK;
 }
 

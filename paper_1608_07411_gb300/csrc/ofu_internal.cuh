@@ -224,13 +224,17 @@ struct LeafSets {
   int n_list = 0;
 };
 
-// Divergence records of the primal step's heavy and list leaves, rebuilt with
-// the leaf classes (solve.cu).  Group position g runs over the heavy set, then
-// the list set.  The -face neighbours of position g are the records
-// start[g] .. start[g + 1] - 1: rec = neighbour index | axis << 28, w = its
-// weight (h_n^3 / h^3) alpha_nl / Delta; cp[3 g + d] is the sum of
-// alpha / Delta over the neighbours across the +d face.
-struct DivRecs {
+// Neighbour records of the heavy and list leaves, rebuilt with the leaf
+// classes (solve.cu): the operator entries of those leaves as flat lists, so
+// the iteration kernels read them before griddepcontrol.wait instead of
+// walking the face lists after it.  Group position g runs over the heavy
+// set, then the list set.  Its neighbours are the records start[g] ..
+// start[g + 1] - 1, rec = neighbour index | axis << 28 and w = the weight:
+//   dual step (gradient)     +face neighbours, alpha / Delta;
+//   primal step (divergence) -face neighbours, (h_n^3 / h^3) alpha_nl / Delta,
+//                            and cp[3 g + d], the sum of alpha / Delta over
+//                            the neighbours across the +d face.
+struct NbrRecs {
   const uint32_t* start = nullptr;
   const uint32_t* rec = nullptr;
   const float* w = nullptr;
@@ -453,20 +457,21 @@ cudaError_t launch_copy_kept_samples(const int32_t* src, int64_t n, const uint32
 // Solver kernels.  `ls` names the heavy leaves and the list leaves of the
 // step (see LeafSets).
 cudaError_t launch_dual(View v, const float* ubar, float* p, const float* sigma, float lambda,
-                        LeafSets ls, cudaStream_t s);
+                        LeafSets ls, NbrRecs gr, cudaStream_t s);
 // p = lambda g / |g| where |g| >= g0 (g the gradient of u), else 0.
 cudaError_t launch_dual_init(View v, const float* u, float* p, float lambda, float g0,
-                             LeafSets ls, cudaStream_t s);
+                             LeafSets ls, NbrRecs gr, cudaStream_t s);
 cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const float* tau,
                           const uint32_t* soff, const void* samp, bool fp16, float gamma,
-                          uint16_t* khint, LeafSets ls, DivRecs dr, cudaStream_t s);
-// Divergence records of the primal leaf sets: counts per group position
-// (cnt[0 .. n_heavy + n_list)), then, with start = their exclusive scan, the
-// records.  rec / w need at least the scanned total, which is at most the
-// list entries plus three per group leaf.
-cudaError_t launch_div_count(View v, LeafSets ls, uint32_t* cnt, cudaStream_t s);
-cudaError_t launch_div_fill(View v, LeafSets ls, const uint32_t* start, uint32_t* rec, float* w,
-                            float* cp, cudaStream_t s);
+                          uint16_t* khint, LeafSets ls, NbrRecs dr, cudaStream_t s);
+// Neighbour records of a leaf set (plus: the dual step's gradient records,
+// else the primal step's divergence records with cp): counts per group
+// position (cnt[0 .. n_heavy + n_list)), then, with start = their exclusive
+// scan, the records.  rec / w need at least the scanned total, which is at
+// most the list entries plus three per group leaf.
+cudaError_t launch_recs_count(View v, LeafSets ls, bool plus, uint32_t* cnt, cudaStream_t s);
+cudaError_t launch_recs_fill(View v, LeafSets ls, bool plus, const uint32_t* start, uint32_t* rec,
+                             float* w, float* cp, cudaStream_t s);
 // SMs of the current device (looked up once per process; build.cu).
 int sm_count();
 size_t energy_tmp_bytes(int64_t n);

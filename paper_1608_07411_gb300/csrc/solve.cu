@@ -53,20 +53,6 @@ __device__ __forceinline__ void dual_finish(float* __restrict__ p, size_t st, in
   p[2 * st + l] = r2;
 }
 
-// Gradient of ubar at leaf l over its +face slots, this lane's share of a
-// group of G lanes (every neighbour term alpha (ubar_m - ubar_l) / Delta).
-__device__ __forceinline__ void grad_share(const View& v, const float* __restrict__ ubar, int64_t l,
-                                           const int32_t e[3], float h, float ul, int lane, int G,
-                                           float acc[3]) {
-  acc[0] = acc[1] = acc[2] = 0.0f;
-  for_each_slot<3>(v, e, lane, G, [&](int f, int32_t ent) {
-    const float t = plus_weight(h, edge_f(v.D, entry_level(ent))) * (ubar[entry_idx(ent)] - ul);
-    acc[0] += f == 0 ? t : 0.0f;
-    acc[1] += f == 1 ? t : 0.0f;
-    acc[2] += f == 2 ? t : 0.0f;
-  });
-}
-
 // Lanes per list leaf of the dual and primal steps (measured over 1..16: 4
 // and 2 fastest on the 256^3 and 512^3 workloads; the primal step has about
 // twice as many list leaves, six faces and its prox).
@@ -82,31 +68,61 @@ __device__ __host__ __forceinline__ int heavy_blocks(const Segments& sg) {
   return (sg.n_heavy * kHeavyLanes + kThreads - 1) / kThreads;
 }
 
+// Records a lane loads before the wait (G lanes per leaf cover G times this
+// many neighbours in the first round).
+constexpr int kRecBatch = 4;
+
 // A dual step of the leaves of a compacted set (heavy or list leaves), G
-// lanes per leaf: the j-th leaf of `set` for threads j G .. j G + G - 1 of
-// the segment starting at block 0 + `b`.  Lanes past the end take the last
-// leaf and do not write (every lane of the warp joins the shuffles).
+// lanes per leaf: the j-th leaf of `set` (group position g0 + j) for threads
+// j G .. j G + G - 1 of the segment starting at block 0 + `b`.  The leaf's
+// +face neighbours come from its gradient records (static between
+// restructures, so read before the wait); after it the lanes gather ubar at
+// the neighbours and the group sums each axis.  Lanes past the end take the
+// last leaf and do not write (every lane of the warp joins the shuffles).
 template <bool INIT, int G>
 __device__ __forceinline__ void dual_group(const View& v, const float* __restrict__ ubar,
                                            float* __restrict__ p, const float* __restrict__ sigma,
-                                           float lambda, float g0, const uint32_t* __restrict__ set,
-                                           int n_set, int b) {
+                                           float lambda, float gth, const NbrRecs& gr,
+                                           const uint32_t* __restrict__ set, int n_set, int g0,
+                                           int b) {
   const size_t st = size_t(v.stride);
   const int t = b * kThreads + int(threadIdx.x);
   const int j = t / G, lane = t % G;
   const bool valid = j < n_set;
-  const int64_t l = set[valid ? j : n_set - 1];
-  const int32_t e[3] = {v.nbr[l], v.nbr[st + l], v.nbr[2 * st + l]};
-  const float h = edge_f(v.D, v.level[l]);
-  const float ul = ubar[l];
-  float acc[3];
-  grad_share(v, ubar, l, e, h, ul, lane, G, acc);
-  float g[3];
+  const int jc = valid ? j : n_set - 1;
+  const int64_t l = set[jc];
+  const int g = g0 + jc;
+  const uint32_t m0 = gr.start[g], m1 = gr.start[g + 1];
+  const float sl = INIT ? 0.0f : sigma[l];
+  uint32_t rec[kRecBatch];
+  float w[kRecBatch];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) g[d] = group_sum<G>(acc[d]);
+  for (int r = 0; r < kRecBatch; ++r) {
+    const uint32_t k = m0 + lane + r * G;
+    rec[r] = k < m1 ? gr.rec[k] : 0u;
+    w[r] = k < m1 ? gr.w[k] : 0.0f;
+  }
+  grid_dep_wait();
+  grid_dep_launch();
+  const float ul = ubar[l];
+  float acc[3] = {0.0f, 0.0f, 0.0f};
+  auto add = [&](uint32_t rk, float wk) {
+    const float tk = wk * (ubar[rk & 0x0fffffffu] - ul);
+    const uint32_t d = rk >> 28;
+    acc[0] += d == 0 ? tk : 0.0f;
+    acc[1] += d == 1 ? tk : 0.0f;
+    acc[2] += d == 2 ? tk : 0.0f;
+  };
+#pragma unroll
+  for (int r = 0; r < kRecBatch; ++r) add(rec[r], w[r]);
+#pragma unroll 4
+  for (uint32_t k = m0 + lane + kRecBatch * G; k < m1; k += G) add(gr.rec[k], gr.w[k]);
+  float gv[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) gv[d] = group_sum<G>(acc[d]);
   if (lane != 0 || !valid) return;
   const float q[3] = {p[l], p[st + l], p[2 * st + l]};
-  dual_finish<INIT>(p, st, l, q, INIT ? 0.0f : sigma[l], g, lambda, g0);
+  dual_finish<INIT>(p, st, l, q, sl, gv, lambda, gth);
 }
 
 // INIT = false: the dual step p <- proj(p + sigma grad ubar).
@@ -118,18 +134,18 @@ template <bool INIT>
 __global__ void __launch_bounds__(kThreads, kIterMinBlocks) k_dual(View v, const float* __restrict__ ubar,
                                                                    float* __restrict__ p,
                                                                    const float* __restrict__ sigma,
-                                                                   float lambda, Segments sg, float g0) {
+                                                                   float lambda, Segments sg, float g0,
+                                                                   NbrRecs gr) {
   const size_t st = size_t(v.stride);
   const int hb = heavy_blocks(sg);
   const int lb = (sg.n_list * kDualListLanes + kThreads - 1) / kThreads;
   const int b = int(blockIdx.x);
   if (b < hb + lb) {
-    grid_dep_wait();
-    grid_dep_launch();
     if (b < hb)
-      dual_group<INIT, kHeavyLanes>(v, ubar, p, sigma, lambda, g0, sg.heavy, sg.n_heavy, b);
+      dual_group<INIT, kHeavyLanes>(v, ubar, p, sigma, lambda, g0, gr, sg.heavy, sg.n_heavy, 0, b);
     else
-      dual_group<INIT, kDualListLanes>(v, ubar, p, sigma, lambda, g0, sg.list, sg.n_list, b - hb);
+      dual_group<INIT, kDualListLanes>(v, ubar, p, sigma, lambda, g0, gr, sg.list, sg.n_list,
+                                       sg.n_heavy, b - hb);
     return;
   }
   const int lbase = hb + lb;
@@ -298,10 +314,6 @@ __device__ __forceinline__ void primal_light(const View& v, float* __restrict__ 
   khint[l] = uint16_t(ks);
 }
 
-// Records a lane loads before the wait (G lanes per leaf cover G times this
-// many -face neighbours in the first round).
-constexpr int kDivRecBatch = 4;
-
 // A primal step of the leaves of a compacted set (heavy or list leaves), G
 // lanes per leaf: the j-th leaf of `set` (group position g0 + j) for threads
 // j G .. j G + G - 1 of the segment starting at block 0 + `b`.  The leaf's
@@ -316,7 +328,7 @@ __device__ __forceinline__ void primal_group(const View& v, float* __restrict__ 
                                              const float* __restrict__ tau,
                                              const uint32_t* __restrict__ soff,
                                              const T* __restrict__ samp, float gamma,
-                                             uint16_t* __restrict__ khint, const DivRecs& dr,
+                                             uint16_t* __restrict__ khint, const NbrRecs& dr,
                                              const uint32_t* __restrict__ set, int n_set, int g0,
                                              int b) {
   const size_t st = size_t(v.stride);
@@ -333,10 +345,10 @@ __device__ __forceinline__ void primal_group(const View& v, float* __restrict__ 
   const float tl = tau[l];
   const uint32_t o = soff[l];
   const int W = int(soff[l + 1] - o);
-  uint32_t rec[kDivRecBatch];
-  float w[kDivRecBatch];
+  uint32_t rec[kRecBatch];
+  float w[kRecBatch];
 #pragma unroll
-  for (int r = 0; r < kDivRecBatch; ++r) {
+  for (int r = 0; r < kRecBatch; ++r) {
     const uint32_t k = m0 + lane + r * G;
     rec[r] = k < m1 ? dr.rec[k] : 0u;
     w[r] = k < m1 ? dr.w[k] : 0.0f;
@@ -345,10 +357,10 @@ __device__ __forceinline__ void primal_group(const View& v, float* __restrict__ 
   grid_dep_launch();
   float acc = 0.0f;
 #pragma unroll
-  for (int r = 0; r < kDivRecBatch; ++r)
+  for (int r = 0; r < kRecBatch; ++r)
     acc += w[r] * p[size_t(rec[r] >> 28) * st + (rec[r] & 0x0fffffffu)];
 #pragma unroll 4
-  for (uint32_t k = m0 + lane + kDivRecBatch * G; k < m1; k += G) {
+  for (uint32_t k = m0 + lane + kRecBatch * G; k < m1; k += G) {
     const uint32_t rk = dr.rec[k];
     acc += dr.w[k] * p[size_t(rk >> 28) * st + (rk & 0x0fffffffu)];
   }
@@ -366,47 +378,59 @@ __device__ __forceinline__ void primal_group(const View& v, float* __restrict__ 
   khint[l] = uint16_t(ks);
 }
 
-// Divergence records (see DivRecs): counts, then records and +face sums.
-__global__ void k_div_count(View v, LeafSets ls, uint32_t* __restrict__ cnt) {
+// Neighbour records (see NbrRecs) of a leaf set: PLUS the +face neighbours
+// with alpha / Delta (gradient of the dual step), else the -face neighbours
+// with (h_n^3 / h^3) alpha_nl / Delta and the +face weight sums (divergence
+// of the primal step).  Counts first, then the records.
+template <bool PLUS>
+__global__ void k_recs_count(View v, LeafSets ls, uint32_t* __restrict__ cnt) {
   const int g = int(blockIdx.x) * blockDim.x + int(threadIdx.x);
   if (g >= ls.n_heavy + ls.n_list) return;
   const int64_t l = g < ls.n_heavy ? ls.heavy[g] : ls.list[g - ls.n_heavy];
   uint32_t c = 0;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const int32_t e = v.nbr[int64_t(3 + d) * v.stride + l];
+    const int32_t e = v.nbr[int64_t(PLUS ? d : 3 + d) * v.stride + l];
     c += e >= 0 ? 1u : (e == kEmpty ? 0u : uint32_t(v.ovf[list_start(e)]));
   }
   cnt[g] = c;
 }
 
-__global__ void k_div_fill(View v, LeafSets ls, const uint32_t* __restrict__ start,
-                           uint32_t* __restrict__ rec, float* __restrict__ w,
-                           float* __restrict__ cp) {
+template <bool PLUS>
+__global__ void k_recs_fill(View v, LeafSets ls, const uint32_t* __restrict__ start,
+                            uint32_t* __restrict__ rec, float* __restrict__ w,
+                            float* __restrict__ cp) {
   const int g = int(blockIdx.x) * blockDim.x + int(threadIdx.x);
   if (g >= ls.n_heavy + ls.n_list) return;
   const int64_t l = g < ls.n_heavy ? ls.heavy[g] : ls.list[g - ls.n_heavy];
   const float h = edge_f(v.D, v.level[l]);
+  if (!PLUS) {
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int32_t e = v.nbr[int64_t(d) * v.stride + l];
-    float sum = 0.0f;
-    if (e >= 0) {
-      sum = plus_weight(h, edge_f(v.D, entry_level(e)));
-    } else if (e != kEmpty) {
-      const uint32_t s0 = list_start(e);
-      const int c = v.ovf[s0];
-      for (int k = 0; k < c; ++k) sum += plus_weight(h, edge_f(v.D, entry_level(v.ovf[s0 + 1 + k])));
+    for (int d = 0; d < 3; ++d) {
+      const int32_t e = v.nbr[int64_t(d) * v.stride + l];
+      float sum = 0.0f;
+      if (e >= 0) {
+        sum = plus_weight(h, edge_f(v.D, entry_level(e)));
+      } else if (e != kEmpty) {
+        const uint32_t s0 = list_start(e);
+        const int c = v.ovf[s0];
+        for (int k = 0; k < c; ++k)
+          sum += plus_weight(h, edge_f(v.D, entry_level(v.ovf[s0 + 1 + k])));
+      }
+      cp[3 * g + d] = sum;
     }
-    cp[3 * g + d] = sum;
   }
+  auto weight = [&](int32_t f) {
+    const float hm = edge_f(v.D, entry_level(f));
+    return PLUS ? plus_weight(h, hm) : minus_weight(h, hm);
+  };
   uint32_t k = start[g];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const int32_t e = v.nbr[int64_t(3 + d) * v.stride + l];
+    const int32_t e = v.nbr[int64_t(PLUS ? d : 3 + d) * v.stride + l];
     if (e >= 0) {
       rec[k] = entry_idx(e) | (uint32_t(d) << 28);
-      w[k] = minus_weight(h, edge_f(v.D, entry_level(e)));
+      w[k] = weight(e);
       ++k;
     } else if (e != kEmpty) {
       const uint32_t s0 = list_start(e);
@@ -414,7 +438,7 @@ __global__ void k_div_fill(View v, LeafSets ls, const uint32_t* __restrict__ sta
       for (int i = 0; i < c; ++i) {
         const int32_t f = v.ovf[s0 + 1 + i];
         rec[k] = entry_idx(f) | (uint32_t(d) << 28);
-        w[k] = minus_weight(h, edge_f(v.D, entry_level(f)));
+        w[k] = weight(f);
         ++k;
       }
     }
@@ -430,7 +454,7 @@ __global__ void __launch_bounds__(kThreads, kIterMinBlocks) k_primal(View v, flo
                                                                      const T* __restrict__ samp,
                                                                      float gamma,
                                                                      uint16_t* __restrict__ khint,
-                                                                     Segments sg, DivRecs dr) {
+                                                                     Segments sg, NbrRecs dr) {
   const int hb = heavy_blocks(sg);
   const int lb = (sg.n_list * kPrimalListLanes + kThreads - 1) / kThreads;
   const int b = int(blockIdx.x);
@@ -872,27 +896,28 @@ inline unsigned grid_of(int64_t n, const Segments& sg, int list_lanes, int light
 }
 
 cudaError_t launch_dual(View v, const float* ubar, float* p, const float* sigma, float lambda,
-                        LeafSets ls, cudaStream_t s) {
+                        LeafSets ls, NbrRecs gr, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
   const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
   const cudaError_t e = launch_iter(k_dual<false>, grid_of(v.n, sg, kDualListLanes, kDualLightLeaves),
-                                    s, v, ubar, p, sigma, lambda, sg, 0.0f);
+                                    s, v, ubar, p, sigma, lambda, sg, 0.0f, gr);
   count_launches(1);
   return e;
 }
 
 cudaError_t launch_dual_init(View v, const float* u, float* p, float lambda, float g0, LeafSets ls,
-                             cudaStream_t s) {
+                             NbrRecs gr, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
   const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
-  k_dual<true><<<grid_of(v.n, sg, kDualListLanes, kDualLightLeaves), kThreads, 0, s>>>(v, u, p, nullptr, lambda, sg, g0);
+  k_dual<true><<<grid_of(v.n, sg, kDualListLanes, kDualLightLeaves), kThreads, 0, s>>>(v, u, p, nullptr,
+                                                                                        lambda, sg, g0, gr);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const float* tau,
                           const uint32_t* soff, const void* samp, bool fp16, float gamma,
-                          uint16_t* khint, LeafSets ls, DivRecs dr, cudaStream_t s) {
+                          uint16_t* khint, LeafSets ls, NbrRecs dr, cudaStream_t s) {
   if (v.n <= 0) return cudaSuccess;
   const Segments sg{ls.heavy, ls.n_heavy, ls.list, ls.n_list};
   const unsigned nb = grid_of(v.n, sg, kPrimalListLanes, 1);
@@ -905,19 +930,25 @@ cudaError_t launch_primal(View v, float* u, float* ubar, const float* p, const f
   return e;
 }
 
-cudaError_t launch_div_count(View v, LeafSets ls, uint32_t* cnt, cudaStream_t s) {
+cudaError_t launch_recs_count(View v, LeafSets ls, bool plus, uint32_t* cnt, cudaStream_t s) {
   const int ng = ls.n_heavy + ls.n_list;
   if (ng == 0) return cudaSuccess;
-  k_div_count<<<blocks_for(ng, kThreads), kThreads, 0, s>>>(v, ls, cnt);
+  if (plus)
+    k_recs_count<true><<<blocks_for(ng, kThreads), kThreads, 0, s>>>(v, ls, cnt);
+  else
+    k_recs_count<false><<<blocks_for(ng, kThreads), kThreads, 0, s>>>(v, ls, cnt);
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_div_fill(View v, LeafSets ls, const uint32_t* start, uint32_t* rec, float* w,
-                            float* cp, cudaStream_t s) {
+cudaError_t launch_recs_fill(View v, LeafSets ls, bool plus, const uint32_t* start, uint32_t* rec,
+                             float* w, float* cp, cudaStream_t s) {
   const int ng = ls.n_heavy + ls.n_list;
   if (ng == 0) return cudaSuccess;
-  k_div_fill<<<blocks_for(ng, kThreads), kThreads, 0, s>>>(v, ls, start, rec, w, cp);
+  if (plus)
+    k_recs_fill<true><<<blocks_for(ng, kThreads), kThreads, 0, s>>>(v, ls, start, rec, w, cp);
+  else
+    k_recs_fill<false><<<blocks_for(ng, kThreads), kThreads, 0, s>>>(v, ls, start, rec, w, cp);
   count_launches(1);
   return cudaGetLastError();
 }
