@@ -396,13 +396,18 @@ __global__ void k_recs_count(View v, LeafSets ls, uint32_t* __restrict__ cnt) {
   cnt[g] = c;
 }
 
+// A warp per group position: lanes share each face list (records written
+// in list order, the +face weight sums reduced in a fixed order).
 template <bool PLUS>
 __global__ void k_recs_fill(View v, LeafSets ls, const uint32_t* __restrict__ start,
                             uint32_t* __restrict__ rec, float* __restrict__ w,
                             float* __restrict__ cp) {
-  const int g = int(blockIdx.x) * blockDim.x + int(threadIdx.x);
-  if (g >= ls.n_heavy + ls.n_list) return;
+  const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = int(threadIdx.x & 31);
+  if (gw >= ls.n_heavy + ls.n_list) return;   // the whole warp
+  const int g = int(gw);
   const int64_t l = g < ls.n_heavy ? ls.heavy[g] : ls.list[g - ls.n_heavy];
+  const int32_t* __restrict__ ovf = v.ovf;
   const float h = edge_f(v.D, v.level[l]);
   if (!PLUS) {
 #pragma unroll
@@ -410,37 +415,39 @@ __global__ void k_recs_fill(View v, LeafSets ls, const uint32_t* __restrict__ st
       const int32_t e = v.nbr[int64_t(d) * v.stride + l];
       float sum = 0.0f;
       if (e >= 0) {
-        sum = plus_weight(h, edge_f(v.D, entry_level(e)));
+        if (lane == 0) sum = plus_weight(h, edge_f(v.D, entry_level(e)));
       } else if (e != kEmpty) {
         const uint32_t s0 = list_start(e);
-        const int c = v.ovf[s0];
-        for (int k = 0; k < c; ++k)
-          sum += plus_weight(h, edge_f(v.D, entry_level(v.ovf[s0 + 1 + k])));
+        const int c = ovf[s0];
+        for (int k = lane; k < c; k += 32) sum += plus_weight(h, edge_f(v.D, entry_level(ovf[s0 + 1 + k])));
       }
-      cp[3 * g + d] = sum;
+      sum = group_sum<32>(sum);
+      if (lane == 0) cp[3 * g + d] = sum;
     }
   }
   auto weight = [&](int32_t f) {
     const float hm = edge_f(v.D, entry_level(f));
     return PLUS ? plus_weight(h, hm) : minus_weight(h, hm);
   };
-  uint32_t k = start[g];
+  uint32_t k0 = start[g];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int32_t e = v.nbr[int64_t(PLUS ? d : 3 + d) * v.stride + l];
     if (e >= 0) {
-      rec[k] = entry_idx(e) | (uint32_t(d) << 28);
-      w[k] = weight(e);
-      ++k;
+      if (lane == 0) {
+        rec[k0] = entry_idx(e) | (uint32_t(d) << 28);
+        w[k0] = weight(e);
+      }
+      k0 += 1;
     } else if (e != kEmpty) {
       const uint32_t s0 = list_start(e);
-      const int c = v.ovf[s0];
-      for (int i = 0; i < c; ++i) {
-        const int32_t f = v.ovf[s0 + 1 + i];
-        rec[k] = entry_idx(f) | (uint32_t(d) << 28);
-        w[k] = weight(f);
-        ++k;
+      const int c = ovf[s0];
+      for (int i = lane; i < c; i += 32) {
+        const int32_t f = ovf[s0 + 1 + i];
+        rec[k0 + i] = entry_idx(f) | (uint32_t(d) << 28);
+        w[k0 + i] = weight(f);
       }
+      k0 += uint32_t(c);
     }
   }
 }
@@ -945,10 +952,11 @@ cudaError_t launch_recs_fill(View v, LeafSets ls, bool plus, const uint32_t* sta
                              float* w, float* cp, cudaStream_t s) {
   const int ng = ls.n_heavy + ls.n_list;
   if (ng == 0) return cudaSuccess;
+  const unsigned nb = blocks_for(int64_t(ng) * 32, kThreads);
   if (plus)
-    k_recs_fill<true><<<blocks_for(ng, kThreads), kThreads, 0, s>>>(v, ls, start, rec, w, cp);
+    k_recs_fill<true><<<nb, kThreads, 0, s>>>(v, ls, start, rec, w, cp);
   else
-    k_recs_fill<false><<<blocks_for(ng, kThreads), kThreads, 0, s>>>(v, ls, start, rec, w, cp);
+    k_recs_fill<false><<<nb, kThreads, 0, s>>>(v, ls, start, rec, w, cp);
   count_launches(1);
   return cudaGetLastError();
 }
