@@ -442,12 +442,13 @@ ofu_status ofu_profile(ofu_ctx* ctx, int32_t enable);
  * through the cache are not counted):
  *   dual   45 B per leaf: ubar, level, three +face entries, p read and
  *          written, sigma;
- *   primal 93 B per leaf: u read and written, ubar written, level, six
- *          face entries, p, tau, sample offset (57 B); the leaf's prox hint
- *          read and written (4 B); one 32-byte sector of samples, the least
- *          a read of the two samples that bracket the prox can move (the
- *          search starts at the previous iteration's rank, so a settled leaf
- *          reads those two and no others).
+ *   primal 57 B per leaf + each observed sample (4 B, or 2 B in float16):
+ *          u read and written, ubar written, level, six face entries, p,
+ *          tau, sample offset, and the samples the prox is defined over.
+ *          The kernel's search starts at the leaf's rank of the previous
+ *          iteration, so a settled leaf reads only the two samples that
+ *          bracket its prox (one 32-byte sector) and the DRAM bytes fall
+ *          below this count.
  * Any output pointer may be NULL. */
 ofu_status ofu_profile_read(ofu_ctx* ctx, double* ms, int64_t* launches, double* bytes);
 

@@ -710,7 +710,7 @@ ofu_status ofu_iterate(ofu_ctx* ctx, int32_t n) {
       ctx->prof_launches[0] += 1;
       ctx->prof_launches[1] += 1;
       ctx->prof_bytes[0] += 45.0 * double(ctx->n);
-      ctx->prof_bytes[1] += 93.0 * double(ctx->n);
+      ctx->prof_bytes[1] += 57.0 * double(ctx->n) + double(ctx->n_samples) * double(sample_bytes(ctx));
     }
   }
   return OFU_OK;

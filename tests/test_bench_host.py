@@ -1,5 +1,6 @@
 """Host-side logic of bench.py on CPU: the clock record, the traffic scaling
-rule, the peak's source and the reference arm's JSON line (no GPU)."""
+rule, the roofline figures, the peak's source and the reference arm's JSON
+line (no GPU)."""
 import json
 import types
 
@@ -62,6 +63,24 @@ def test_traffic_is_scaled_and_dropped_when_the_kernel_changes(monkeypatch):
     monkeypatch.setattr(bench, "kernel_source_sha", lambda: "0" * 16)
     assert bench.measured_traffic("k_primal", wl, rec["alg_bytes_per_launch"]) is None
     assert bench.measured_traffic("no_such_kernel", wl, 1.0) is None
+
+
+def test_roofline_of_the_dominant_kernel_and_the_primal_least_bytes(monkeypatch):
+    monkeypatch.setattr(bench, "peak_hbm", lambda: (6000.0, "measured"))
+    monkeypatch.setattr(bench, "measured_traffic", lambda *a: None)
+    # 10 iterations of 1e6 leaves: dual 2 ms, primal 5 ms in all
+    res = {"profile": {"ms": [2.0, 5.0], "launches": [10, 10], "alg_bytes": [45e7, 2.1e9],
+                       "leaf_iterations": 1e7}}
+    r = bench.roofline(res, "at_scale")
+    assert r["kernel"] == "k_primal" and r["launches"] == 10
+    assert r["achieved"] == pytest.approx(2.1e9 / 5e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6000.0)
+    assert r["alg_bytes_per_launch"] == pytest.approx(2.1e8) and r["avg_launch_us"] == pytest.approx(500.0)
+    assert r["other"]["kernel"] == "k_dual" and r["other"]["achieved"] == pytest.approx(225.0)
+    m = r["k_primal_min_bytes"]
+    assert m["bytes_per_leaf"] == 93
+    assert m["achieved"] == pytest.approx(93 * 1e7 / 5e-3 / 1e9)
+    assert m["frac"] == pytest.approx(m["achieved"] / 6000.0)
 
 
 def test_peak_from_measured_file_else_fallback(monkeypatch, tmp_path):
